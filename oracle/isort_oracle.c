@@ -1,0 +1,350 @@
+/*
+ * ORACLE — test infrastructure only.
+ *
+ * A plain, serial, obviously-correct CPU restatement of what the integer-sort
+ * hot path computes. Only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg may load this library; the product path never does.
+ * It shares no code, header or table with the CUDA library.
+ *
+ * Definition of the result (every entry point): the stable sort of the
+ * (key, payload) pairs by unsigned key, i.e. ascending by (key, original
+ * index). Integer keys have exactly one such output.
+ *
+ * Functions and the passages they follow (Gerbessiotis, "Integer sorting on
+ * multicores: some (experiments and) observations", arXiv:1708.09495):
+ *   oracle_count_round_*  one count-sort round: count, prefix, ordered output
+ *                         (Section 3, "Serial radix-r radix-sort", eq. Ts)
+ *   oracle_lsd_*          SR4 generalised: ceil(key_bits / radix_bits) rounds,
+ *                         least significant digit first (Section 3, eq. Ts;
+ *                         fewer rounds for a known key range, Section 1 and
+ *                         Section 2's remarks on bounded key values)
+ *   oracle_digit_hist_*   the count step of every round, for all rounds
+ *   oracle_btn_u32        BTN: p sorted blocks + lg p (lg p + 1)/2 merge-split
+ *                         stages of a p-input bitonic network (Section 2; Section 3
+ *                         "Bitonic Sort", eq. Tb)
+ *   oracle_oet_u32        OET: p sorted blocks + p rounds of odd-even
+ *                         transposition with merge-split (Section 2; Section 3
+ *                         "Odd-even transposition sort", eq. To)
+ *   oracle_insertion_*    brute force: stable insertion sort (a pin, not the
+ *                         paper's method)
+ *   oracle_segmented_u32  the LSD sort applied to each CSR segment on its own
+ *   invariant checkers    non-decreasing, stability (payload = index), 64-bit
+ *                         commutative multiset hash
+ *
+ * Readings where the paper is silent:
+ *   - lg r need not divide the key width: the last digit is narrower.
+ *   - BTN/OET compare (key, original index) so that the unique stable order
+ *     comes out; blocks are padded with (max key, index >= n) pads.
+ *   - OET round t pairs blocks (j, j+1) with j = t mod 2, t = 0..p-1.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef ORACLE_MUTANT
+#define ORACLE_MUTANT 0 /* >0 only in the tests' deliberately broken builds */
+#endif
+
+static int num_rounds(int key_bits, int radix_bits) { return (key_bits + radix_bits - 1) / radix_bits; }
+
+/* ------------------------------------------------------------------------
+ * One count-sort round over digit (key >> shift) & (2^width - 1).
+ * Count, exclusive prefix, then the output written in input order, which makes
+ * the round stable (Section 3, Serial radix-r: read for counting, read again
+ * for output, write the output).
+ * ---------------------------------------------------------------------- */
+#define DEFINE_COUNT_ROUND(NAME, KT)                                                                 \
+    int NAME(const KT* kin, const uint32_t* vin, KT* kout, uint32_t* vout, size_t n, int shift,    \
+             int width) {                                                                           \
+        size_t nb = (size_t)1 << width;                                                             \
+        KT mask = (KT)(nb - 1);                                                                     \
+        size_t* count = (size_t*)calloc(nb, sizeof(size_t));                                        \
+        if (!count) return -1;                                                                      \
+        for (size_t i = 0; i < n; ++i) count[(size_t)((kin[i] >> shift) & mask)]++;                  \
+        size_t run = 0;                                                                             \
+        for (size_t b = 0; b < nb; ++b) { size_t c = count[b]; count[b] = run; run += c; }          \
+        if (ORACLE_MUTANT == 1) { /* planted: ties placed from the bucket end (unstable) */        \
+            for (size_t b = 0; b + 1 < nb; ++b) count[b] = count[b + 1];                            \
+            count[nb - 1] = n;                                                                      \
+            for (size_t i = 0; i < n; ++i) {                                                        \
+                size_t d = (size_t)((kin[i] >> shift) & mask);                                      \
+                size_t o = --count[d];                                                              \
+                kout[o] = kin[i];                                                                   \
+                if (vin) vout[o] = vin[i];                                                          \
+            }                                                                                       \
+        } else {                                                                                    \
+            for (size_t i = 0; i < n; ++i) {                                                        \
+                size_t d = (size_t)((kin[i] >> shift) & mask);                                      \
+                size_t o = count[d]++;                                                              \
+                kout[o] = kin[i];                                                                   \
+                if (vin && ORACLE_MUTANT != 2) vout[o] = vin[i];                                    \
+                if (vin && ORACLE_MUTANT == 2) vout[i] = vin[i]; /* planted: payload left behind */ \
+            }                                                                                       \
+        }                                                                                           \
+        free(count);                                                                                \
+        return 0;                                                                                   \
+    }
+
+DEFINE_COUNT_ROUND(oracle_count_round_u32, uint32_t)
+DEFINE_COUNT_ROUND(oracle_count_round_u64, uint64_t)
+
+/* ------------------------------------------------------------------------
+ * LSD radix sort: rounds d = 0..P-1 over digits of radix_bits bits, starting at
+ * the least significant one; P = ceil(key_bits / radix_bits) (Section 3, eq. Ts
+ * with 32/lg r rounds; fewer rounds when keys are known to be < 2^key_bits).
+ * The result overwrites keys/vals. Returns 0, or -1 on bad arguments / memory.
+ * ---------------------------------------------------------------------- */
+#define DEFINE_LSD(NAME, ROUND, KT, KBITS)                                                          \
+    int NAME(KT* keys, uint32_t* vals, size_t n, int key_bits, int radix_bits) {                   \
+        if (key_bits == 0) key_bits = KBITS;                                                        \
+        if (key_bits < 1 || key_bits > KBITS || radix_bits < 1 || radix_bits > 16) return -1;      \
+        if (n <= 1) return 0;                                                                       \
+        KT* k2 = (KT*)malloc(n * sizeof(KT));                                                       \
+        uint32_t* v2 = vals ? (uint32_t*)malloc(n * sizeof(uint32_t)) : NULL;                       \
+        if (!k2 || (vals && !v2)) { free(k2); free(v2); return -1; }                                \
+        KT *ka = keys, *kb = k2;                                                                    \
+        uint32_t *va = vals, *vb = v2;                                                              \
+        int P = num_rounds(key_bits, radix_bits);                                                   \
+        if (ORACLE_MUTANT == 3) P = key_bits / radix_bits; /* planted: short last digit dropped */  \
+        for (int d = 0; d < P; ++d) {                                                               \
+            int shift = d * radix_bits;                                                             \
+            int width = key_bits - shift < radix_bits ? key_bits - shift : radix_bits;              \
+            if (ROUND(ka, va, kb, vb, n, shift, width)) { P = -1; break; }                          \
+            KT* tk = ka; ka = kb; kb = tk;                                                          \
+            uint32_t* tv = va; va = vb; vb = tv;                                                    \
+        }                                                                                           \
+        if (ka != keys) {                                                                           \
+            memcpy(keys, ka, n * sizeof(KT));                                                       \
+            if (vals) memcpy(vals, va, n * sizeof(uint32_t));                                       \
+        }                                                                                           \
+        free(k2); free(v2);                                                                         \
+        return P < 0 ? -1 : 0;                                                                      \
+    }
+
+DEFINE_LSD(oracle_lsd_u32, oracle_count_round_u32, uint32_t, 32)
+DEFINE_LSD(oracle_lsd_u64, oracle_count_round_u64, uint64_t, 64)
+
+/* Per-round digit histograms of the input: hist[d * 2^radix_bits + b] = number
+ * of keys whose round-d digit equals b (the count step of Section 3's
+ * count-sort, taken for all rounds at once; counts are invariant under the
+ * permutations the earlier rounds apply). */
+#define DEFINE_HIST(NAME, KT, KBITS)                                                                \
+    int NAME(const KT* keys, size_t n, int key_bits, int radix_bits, uint64_t* hist) {             \
+        if (key_bits == 0) key_bits = KBITS;                                                        \
+        if (key_bits < 1 || key_bits > KBITS || radix_bits < 1 || radix_bits > 16) return -1;      \
+        int P = num_rounds(key_bits, radix_bits);                                                   \
+        size_t nb = (size_t)1 << radix_bits;                                                        \
+        memset(hist, 0, sizeof(uint64_t) * nb * (size_t)P);                                         \
+        for (int d = 0; d < P; ++d) {                                                               \
+            int shift = d * radix_bits;                                                             \
+            int width = key_bits - shift < radix_bits ? key_bits - shift : radix_bits;              \
+            KT mask = (KT)(((uint64_t)1 << width) - 1);                                             \
+            for (size_t i = 0; i < n; ++i) hist[(size_t)d * nb + (size_t)((keys[i] >> shift) & mask)]++; \
+        }                                                                                           \
+        return P;                                                                                   \
+    }
+
+DEFINE_HIST(oracle_digit_hist_u32, uint32_t, 32)
+DEFINE_HIST(oracle_digit_hist_u64, uint64_t, 64)
+
+/* ------------------------------------------------------------------------
+ * Brute force: stable insertion sort (a pin for the oracle, not the method).
+ * ---------------------------------------------------------------------- */
+#define DEFINE_INSERTION(NAME, KT)                                                                  \
+    void NAME(KT* keys, uint32_t* vals, size_t n) {                                                 \
+        for (size_t i = 1; i < n; ++i) {                                                            \
+            KT k = keys[i];                                                                         \
+            uint32_t v = vals ? vals[i] : 0;                                                        \
+            size_t j = i;                                                                           \
+            while (j > 0 && keys[j - 1] > k) {                                                      \
+                keys[j] = keys[j - 1];                                                              \
+                if (vals) vals[j] = vals[j - 1];                                                    \
+                --j;                                                                                \
+            }                                                                                       \
+            keys[j] = k;                                                                            \
+            if (vals) vals[j] = v;                                                                  \
+        }                                                                                           \
+    }
+
+DEFINE_INSERTION(oracle_insertion_u32, uint32_t)
+DEFINE_INSERTION(oracle_insertion_u64, uint64_t)
+
+/* ------------------------------------------------------------------------
+ * BTN and OET (Section 2; Section 3 eqs. Tb and To).
+ *
+ * Items are (key, original index) pairs compared lexicographically, so ties
+ * resolve to input order and the output is the unique stable order. The n
+ * items are padded to p * m (m = ceil(n/p)) with pads (2^32-1, n + j) that sort
+ * after every real item, split into p blocks of m, and each block is sorted on
+ * its own (the paper's SR4 local sort: here the oracle's LSD round applied to
+ * the composite (key << 32 | index), which sorts by key then index).
+ * Then the network runs with "compare-exchange" replaced by merge-split: the
+ * two sorted blocks are merged and the lower-indexed block keeps the m smallest
+ * (or, for a descending comparator, the m largest).
+ * ---------------------------------------------------------------------- */
+static void merge_split(uint64_t* lo_blk, uint64_t* hi_blk, size_t m, uint64_t* tmp, int lower_keeps_small) {
+    size_t a = 0, b = 0;
+    for (size_t t = 0; t < 2 * m; ++t) {
+        if (b >= m || (a < m && lo_blk[a] <= hi_blk[b])) tmp[t] = lo_blk[a++];
+        else tmp[t] = hi_blk[b++];
+    }
+    if (lower_keeps_small) {
+        memcpy(lo_blk, tmp, m * sizeof(uint64_t));
+        memcpy(hi_blk, tmp + m, m * sizeof(uint64_t));
+    } else {
+        memcpy(lo_blk, tmp + m, m * sizeof(uint64_t));
+        memcpy(hi_blk, tmp, m * sizeof(uint64_t));
+    }
+}
+
+static uint64_t* make_blocks(const uint32_t* keys, size_t n, int p, size_t* m_out) {
+    size_t m = (n + (size_t)p - 1) / (size_t)p;
+    if (m == 0) m = 1;
+    size_t tot = m * (size_t)p;
+    uint64_t* it = (uint64_t*)malloc(tot * sizeof(uint64_t));
+    if (!it) return NULL;
+    for (size_t i = 0; i < tot; ++i)
+        it[i] = i < n ? ((uint64_t)keys[i] << 32) | (uint64_t)i : (0xFFFFFFFFULL << 32) | (uint64_t)i;
+    /* local sort of each block (SR4 over the 64-bit composite) */
+    for (int j = 0; j < p; ++j)
+        if (oracle_lsd_u64(it + (size_t)j * m, NULL, m, 64, 8)) { free(it); return NULL; }
+    *m_out = m;
+    return it;
+}
+
+static void unblock(const uint64_t* it, const uint32_t* keys_in_copy, uint32_t* keys, uint32_t* vals,
+                    const uint32_t* vals_in_copy, size_t n) {
+    /* pads sort last, so the first n items are the real ones */
+    for (size_t i = 0; i < n; ++i) {
+        uint32_t idx = (uint32_t)(it[i] & 0xFFFFFFFFu);
+        keys[i] = keys_in_copy[idx];
+        if (vals) vals[i] = vals_in_copy[idx];
+    }
+}
+
+static int is_pow2(int p) { return p > 0 && (p & (p - 1)) == 0; }
+
+/* BTN: p a power of two. *stages receives the number of merge-split stages
+ * executed, lg p (lg p + 1) / 2. n must be < 2^32. */
+int oracle_btn_u32(uint32_t* keys, uint32_t* vals, size_t n, int p, uint64_t* stages) {
+    if (!is_pow2(p) || n >= ((size_t)1 << 32) - (size_t)p) return -1;
+    uint64_t st = 0;
+    if (n == 0) { if (stages) *stages = 0; return 0; }
+    size_t m;
+    uint64_t* it = make_blocks(keys, n, p, &m);
+    uint32_t* kc = (uint32_t*)malloc(n * sizeof(uint32_t));
+    uint32_t* vc = vals ? (uint32_t*)malloc(n * sizeof(uint32_t)) : NULL;
+    uint64_t* tmp = (uint64_t*)malloc(2 * m * sizeof(uint64_t));
+    if (!it || !kc || (vals && !vc) || !tmp) { free(it); free(kc); free(vc); free(tmp); return -1; }
+    memcpy(kc, keys, n * sizeof(uint32_t));
+    if (vals) memcpy(vc, vals, n * sizeof(uint32_t));
+    /* Bitonic network on p blocks: for merge size k = 2, 4, ..., p and
+     * distance j = k/2, ..., 1, block i pairs with block i ^ j; the pair is in
+     * an ascending comparator iff (i & k) == 0. */
+    for (int k = 2; k <= p; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = 0; i < p; ++i) {
+                int l = i ^ j;
+                if (l <= i) continue;
+                int asc = (i & k) == 0;
+                if (ORACLE_MUTANT == 4) asc = 1; /* planted: direction ignored */
+                merge_split(it + (size_t)i * m, it + (size_t)l * m, m, tmp, asc);
+            }
+            ++st;
+        }
+    }
+    unblock(it, kc, keys, vals, vc, n);
+    if (stages) *stages = st;
+    free(it); free(kc); free(vc); free(tmp);
+    return 0;
+}
+
+/* OET: any p >= 1. *rounds receives the number of transposition rounds, p. */
+int oracle_oet_u32(uint32_t* keys, uint32_t* vals, size_t n, int p, uint64_t* rounds) {
+    if (p < 1 || n >= ((size_t)1 << 32) - (size_t)p) return -1;
+    uint64_t rd = 0;
+    if (n == 0) { if (rounds) *rounds = 0; return 0; }
+    size_t m;
+    uint64_t* it = make_blocks(keys, n, p, &m);
+    uint32_t* kc = (uint32_t*)malloc(n * sizeof(uint32_t));
+    uint32_t* vc = vals ? (uint32_t*)malloc(n * sizeof(uint32_t)) : NULL;
+    uint64_t* tmp = (uint64_t*)malloc(2 * m * sizeof(uint64_t));
+    if (!it || !kc || (vals && !vc) || !tmp) { free(it); free(kc); free(vc); free(tmp); return -1; }
+    memcpy(kc, keys, n * sizeof(uint32_t));
+    if (vals) memcpy(vc, vals, n * sizeof(uint32_t));
+    int R = p;
+    if (ORACLE_MUTANT == 5) R = p - 1; /* planted: one round short */
+    for (int t = 0; t < R; ++t) {
+        for (int j = t & 1; j + 1 < p; j += 2) merge_split(it + (size_t)j * m, it + (size_t)(j + 1) * m, m, tmp, 1);
+        ++rd;
+    }
+    unblock(it, kc, keys, vals, vc, n);
+    if (rounds) *rounds = rd;
+    free(it); free(kc); free(vc); free(tmp);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * Segmented: segment s is [off[s], off[s+1]); each is LSD-sorted on its own.
+ * ---------------------------------------------------------------------- */
+int oracle_segmented_u32(uint32_t* keys, uint32_t* vals, const uint64_t* off, size_t nseg, int key_bits,
+                         int radix_bits) {
+    for (size_t s = 0; s < nseg; ++s) {
+        if (off[s + 1] < off[s]) return -1;
+        size_t len = (size_t)(off[s + 1] - off[s]);
+        if (oracle_lsd_u32(keys + off[s], vals ? vals + off[s] : NULL, len, key_bits, radix_bits)) return -1;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * Invariant checkers.
+ * ---------------------------------------------------------------------- */
+int oracle_is_sorted_u32(const uint32_t* k, size_t n) {
+    for (size_t i = 1; i < n; ++i)
+        if (k[i - 1] > k[i]) return 0;
+    return 1;
+}
+int oracle_is_sorted_u64(const uint64_t* k, size_t n) {
+    for (size_t i = 1; i < n; ++i)
+        if (k[i - 1] > k[i]) return 0;
+    return 1;
+}
+
+/* With payload = original index, a stable sorted output has strictly
+ * increasing payloads inside every run of equal keys. */
+int oracle_is_stable_u32(const uint32_t* k, const uint32_t* v, size_t n) {
+    for (size_t i = 1; i < n; ++i)
+        if (k[i - 1] == k[i] && v[i - 1] >= v[i]) return 0;
+    return 1;
+}
+int oracle_is_stable_u64(const uint64_t* k, const uint32_t* v, size_t n) {
+    for (size_t i = 1; i < n; ++i)
+        if (k[i - 1] == k[i] && v[i - 1] >= v[i]) return 0;
+    return 1;
+}
+
+/* Commutative multiset hash: sum over items of mix(key ^ rotl(val, 32)) mod
+ * 2^64, mix being SplitMix64's bijective finaliser (Steele, Lea & Flood 2014).
+ * Equal multisets of (key, val) pairs give equal sums. */
+static inline uint64_t fmix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+static inline uint64_t rotl32(uint64_t v) { return (v << 32) | (v >> 32); }
+
+uint64_t oracle_multiset_hash_u32(const uint32_t* k, const uint32_t* v, size_t n) {
+    uint64_t h = 0;
+    for (size_t i = 0; i < n; ++i) {
+        uint64_t val = v ? (uint64_t)v[i] : 0;
+        if (ORACLE_MUTANT == 6) val = 0; /* planted: payload ignored */
+        h += fmix((uint64_t)k[i] ^ rotl32(val));
+    }
+    return h;
+}
+uint64_t oracle_multiset_hash_u64(const uint64_t* k, const uint32_t* v, size_t n) {
+    uint64_t h = 0;
+    for (size_t i = 0; i < n; ++i) h += fmix(k[i] ^ rotl32(v ? (uint64_t)v[i] : 0));
+    return h;
+}
