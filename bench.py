@@ -1,0 +1,309 @@
+"""Benchmark: stable LSD radix sort of n = 2^28 uint32 keys (uniform on
+[0, 2^32), seed 2) with a uint32 payload (= original index), radix 2^8
+(4 count-sort rounds), on one GB300.
+
+One step = one sort through the library's out-of-place call (all kernels of
+the path: digit histogram, digit scan, one rank-and-scatter launch per round).
+Inputs stay pristine, so every step does identical work; they are 2 GiB, far
+larger than the 129 MB L2, so no L2 flush is needed between steps.
+
+Prints ONE JSON line (rank 0). ``--impl reference`` times the serial CPU oracle
+instead, on a bounded sample of the same workload, on the host cores.
+Multi-GPU (torchrun): independent replicas, one per GPU (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gkeys/s (u32 n=2^28) & % HBM roofline; learned/batched vs plain LSD, bit-exact"
+UNIT = "Gkeys/s"
+N = 1 << 28
+SEED = 2
+RADIX_BITS = 8
+KEY_BITS = 32
+ROUNDS = 4
+WORKLOAD = ("stable LSD radix sort, u32 keys uniform on [0,2^32) (seed 2) + u32 payload = index, "
+            "n = 2^28, radix 2^8 (4 rounds), out of place")
+# Algorithmic bytes (fixed formula): one key read for the digit counts of all
+# rounds, then per round one read and one write of key + payload.
+BYTES_PER_KEY = 4 + ROUNDS * 2 * (4 + 4)
+ROUND_BYTES_PER_KEY = 2 * (4 + 4)  # one rank-and-scatter launch
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"isort_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        try:
+            for ln in open(self.path):
+                p = [x.strip() for x in ln.split(",")]
+                if len(p) >= 9 and p[1].replace(".", "").isdigit():
+                    rows.append(p)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_inputs():
+    from gen import workloads
+
+    return workloads.large_uniform(N, 32, SEED, payload=True)
+
+
+def cpu_baseline_oracle(keys, vals, sample_n: int, reps: int):
+    """The serial C oracle (1 core) on the first sample_n keys; Gkeys/s."""
+    import oracle
+
+    k, v = keys[:sample_n].copy(), vals[:sample_n].copy()
+    oracle.lsd(k[:1024], v[:1024], KEY_BITS, RADIX_BITS)  # load + warm
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.lsd(k, v, KEY_BITS, RADIX_BITS)
+        times.append(time.perf_counter() - t0)
+    t = statistics.median(times)
+    return sample_n / t / 1e9, t, times
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    keys, vals = make_inputs()
+    sample_n = 1 << 23
+    import oracle
+
+    k, v = keys[:sample_n].copy(), vals[:sample_n].copy()
+    for _ in range(args.warmup):
+        oracle.lsd(k, v, KEY_BITS, RADIX_BITS)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.lsd(k, v, KEY_BITS, RADIX_BITS)
+    dt = time.perf_counter() - t0
+    val = args.steps * sample_n / dt / 1e9
+    sample = f"first 2^23 keys (+payload) of the workload per step, serial oracle, {args.steps} steps"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_n": sample_n, "radix_bits": RADIX_BITS, "key_bits": KEY_BITS},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1708_09495_gb300 as isort
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    lib = isort.load()
+    stream = torch.cuda.current_stream()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+
+    keys, vals = make_inputs()
+    ki = torch.from_numpy(keys.view(np.int32)).cuda()
+    vi = torch.from_numpy(vals.view(np.int32)).cuda()
+    ko, vo = torch.empty_like(ki), torch.empty_like(vi)
+    args_c = [ctypes.c_void_p(ki.data_ptr()), ctypes.c_void_p(vi.data_ptr()), ctypes.c_void_p(ko.data_ptr()),
+              ctypes.c_void_p(vo.data_ptr()), N, KEY_BITS, RADIX_BITS, sp]
+
+    def step():
+        rc = lib.isort_radix_copy(*args_c)
+        if rc != 0:
+            raise RuntimeError(f"isort_radix_copy failed: {isort.STATUS.get(rc, rc)}")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # correctness spot check of the bench's own output (sorted + stable)
+    sk = ko[:: N // 4096].cpu().numpy().view(np.uint32)
+    if not np.all(sk[1:] >= sk[:-1]):
+        raise RuntimeError("bench output not sorted")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    isort.profile_read()  # clear
+    launches0 = isort.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    isort.profile_enable(True)
+    with ClockSampler(local) as clk:
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        barrier()
+    isort.profile_enable(False)
+    launches = isort.launch_count() - launches0
+    ms = e0.elapsed_time(e1)
+    prof = isort.profile_read()
+    ms_t = torch.tensor([ms], device="cuda")
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * args.steps * N / (ms_max * 1e-3) / 1e9
+
+    # dominant kernel: the rank-and-scatter round
+    peak, peak_kind = peaks()
+    rl, rms = prof.get("onesweep", (0, 0.0))
+    avg_round_ms = rms / max(rl, 1)
+    achieved = N * ROUND_BYTES_PER_KEY / (avg_round_ms * 1e-3) / 1e9 if rl else None
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "onesweep_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            with open(tpath) as f:
+                traffic = json.load(f).get("bytes_per_launch")
+        except Exception:
+            traffic = None
+    kernels = {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in prof.items()}
+
+    # end to end: host (pinned) buffers through the same C call, copies included
+    e2e = None
+    if not args.no_e2e:
+        hk = torch.from_numpy(keys.view(np.int32)).pin_memory()
+        hv = torch.from_numpy(vals.view(np.int32)).pin_memory()
+        hko = torch.empty_like(hk).pin_memory()
+        hvo = torch.empty_like(hv).pin_memory()
+        hargs = [ctypes.c_void_p(hk.data_ptr()), ctypes.c_void_p(hv.data_ptr()), ctypes.c_void_p(hko.data_ptr()),
+                 ctypes.c_void_p(hvo.data_ptr()), N, KEY_BITS, RADIX_BITS, sp]
+        for _ in range(2):
+            assert lib.isort_radix_copy(*hargs) == 0
+        e2e_steps = max(1, min(args.steps, 5))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            rc = lib.isort_radix_copy(*hargs)
+            if rc != 0:
+                raise RuntimeError(f"e2e failed: {rc}")
+        barrier()
+        dt = time.perf_counter() - t0
+        e2e = {"value": world * e2e_steps * N / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": N * 8,
+               "d2h_bytes_per_step": N * 8, "steps": e2e_steps}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, t, times = cpu_baseline_oracle(keys, vals, 1 << 24, 3)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "first 2^24 keys (+payload) of the workload, serial C oracle, median of 3 runs"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N, "key_bits": KEY_BITS, "radix_bits": RADIX_BITS,
+                       "payload": "u32 index", "l2": "inputs (2 GiB) larger than L2; no flush",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                         "kernel": "onesweep (one count-sort round)", "peak_kind": peak_kind,
+                         "whole_sort_frac": N * BYTES_PER_KEY / (ms_max / args.steps * 1e-3) / 1e9 / peak},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "kernels": kernels,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

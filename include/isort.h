@@ -1,0 +1,177 @@
+/*
+ * isort — GB300 (sm_103a) integer sorting: the count-sort rounds of LSD radix
+ * sort, the BTN and OET block networks, a batched segmented sort and a
+ * learned-bucket sort, behind a plain C ABI.
+ *
+ * Method: A. V. Gerbessiotis, "Integer sorting on multicores: some
+ * (experiments and) observations", arXiv:1708.09495. Each entry point names the
+ * section and equation that defines what it computes.
+ *
+ * Common conventions
+ *   - Every sort is STABLE: equal keys keep their input order, so the result
+ *     is the unique order by (key, original index). Keys compare as unsigned.
+ *   - keys / vals are caller-owned buffers of n elements. They may live in
+ *     device memory (cudaMalloc, torch tensors, managed memory) or in host
+ *     memory (pinned or pageable): host buffers are staged through device
+ *     memory inside the call and the call then returns only after the result
+ *     is back in the host buffers. vals == NULL means "keys only"; otherwise
+ *     vals is a uint32 payload that moves with its key.
+ *   - stream is a cudaStream_t (NULL = the legacy default stream). Work is
+ *     enqueued on it. In the default synchronous-status mode (see
+ *     isort_set_sync) the call waits for its own work to finish so that device
+ *     detected errors (ISORT_ERR_KEY_RANGE, ISORT_ERR_TIMEOUT) are returned;
+ *     with isort_set_sync(0) the call returns after enqueueing and those errors
+ *     are collected later with isort_device_status.
+ *   - Scratch memory (ping-pong buffers, digit tables, look-back words) is
+ *     taken stream-ordered from a pool owned by the library on the current
+ *     device and given back at the end of the call; the pool keeps the memory
+ *     for reuse. ISORT_ERR_NO_MEMORY leaves the inputs untouched.
+ *   - key_bits: keys must be < 2^key_bits (1..32 for u32, 1..64 for u64; 0 =
+ *     full width). Fewer key bits mean fewer count-sort rounds. A key outside
+ *     the range is detected before any data moves: ISORT_ERR_KEY_RANGE, buffers
+ *     unchanged.
+ *   - radix_bits: digit width r = 2^radix_bits, 1..16. The number of rounds is
+ *     ceil(key_bits / radix_bits); the last digit is narrower when radix_bits
+ *     does not divide key_bits.
+ *   - n must be < 2^30 (ISORT_ERR_UNSUPPORTED otherwise). n = 0 or 1 returns
+ *     ISORT_OK without touching memory.
+ *   - Argument errors are reported before anything is launched.
+ *   - All functions are thread-safe with respect to each other; concurrent
+ *     calls on different streams use separate scratch memory.
+ */
+#ifndef ISORT_H_
+#define ISORT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ISORT_API __attribute__((visibility("default")))
+#else
+#define ISORT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ISORT_OK = 0,
+    ISORT_ERR_INVALID_ARG = 1, /* a bad size, width, pointer or mode */
+    ISORT_ERR_KEY_RANGE = 2,   /* some key >= 2^key_bits; buffers unchanged */
+    ISORT_ERR_NO_MEMORY = 3,   /* scratch allocation failed; buffers unchanged */
+    ISORT_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+    ISORT_ERR_TIMEOUT = 5,     /* a bounded device wait gave up; contents unspecified */
+    ISORT_ERR_UNSUPPORTED = 6  /* valid but not supported (e.g. size beyond a limit) */
+} isort_status;
+
+/* Human-readable name of a status code (static string). */
+ISORT_API const char* isort_status_string(isort_status s);
+
+/* ---------------------------------------------------------------------------
+ * LSD radix sort (Section 3, "Serial/Parallel radix-r radix-sort", eqs. Ts, Tp:
+ * ceil(key_bits / lg r) rounds of count-sort, least significant digit first).
+ * One read of the keys builds the digit counts of every round; each round then
+ * reads and writes the keys (and payloads) once, ranking keys inside a tile and
+ * resolving tile offsets with a decoupled look-back prefix.
+ * In place: on ISORT_OK keys (and vals) hold the sorted result.
+ * ------------------------------------------------------------------------- */
+ISORT_API isort_status isort_radix(uint32_t* keys, uint32_t* vals, size_t n, int key_bits, int radix_bits, void* stream);
+ISORT_API isort_status isort_radix_u64(uint64_t* keys, uint32_t* vals, size_t n, int key_bits, int radix_bits,
+                                       void* stream);
+
+/* Out-of-place form: the inputs are read, never written; the sorted result goes
+ * to keys_out / vals_out (which must not overlap the inputs). vals_in and
+ * vals_out are both NULL or both non-NULL. Same rounds as isort_radix. */
+ISORT_API isort_status isort_radix_copy(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                              uint32_t* vals_out, size_t n, int key_bits, int radix_bits, void* stream);
+ISORT_API isort_status isort_radix_copy_u64(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
+                                  uint32_t* vals_out, size_t n, int key_bits, int radix_bits, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * The two primitives of a count-sort round (Section 3, "Serial radix-r"), for
+ * callers that drive rounds themselves and for checking each step.
+ *
+ * isort_digit_hist: hist[d * 2^radix_bits + b] = number of keys whose round-d
+ *   digit (key >> d*radix_bits) & (2^w - 1) equals b, for every round d <
+ *   ceil(key_bits / radix_bits) (w = radix_bits, or what is left of key_bits in
+ *   the last round). hist is a DEVICE buffer of rounds * 2^radix_bits uint32
+ *   that the call overwrites. keys is device memory. key_width is 32 or 64.
+ *   Key range violations are reported as ISORT_ERR_KEY_RANGE (hist still
+ *   written).
+ * isort_count_round: one stable count-sort round on the digit
+ *   (key >> shift) & (2^width - 1), width 1..16, out of place: the output is
+ *   ordered by digit, ties in input order. All buffers are device memory.
+ * ------------------------------------------------------------------------- */
+ISORT_API isort_status isort_digit_hist(const void* keys, int key_width, size_t n, int key_bits, int radix_bits,
+                              uint32_t* hist, void* stream);
+ISORT_API isort_status isort_count_round(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                               uint32_t* vals_out, size_t n, int shift, int width, void* stream);
+ISORT_API isort_status isort_count_round_u64(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
+                                   uint32_t* vals_out, size_t n, int shift, int width, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * BTN (Section 2 and Section 3 "Bitonic Sort", eq. Tb): the n keys are split
+ * into p blocks of ceil(n/p), each block is sorted locally, then a p-input
+ * bitonic network of lg p (lg p + 1)/2 stages runs with every comparator
+ * replaced by a merge-split (the lower block keeps the smaller half).
+ * OET (Section 2 and Section 3 "Odd-even transposition sort", eq. To): the same
+ * p sorted blocks, then p rounds of merge-split between neighbouring blocks
+ * (j, j+1), j = round mod 2.
+ * Items compare as (key, original index), which makes the networks stable.
+ * On the GPU a block lives in one thread's registers; one CTA sorts the array.
+ * isort_btn / isort_oet choose p; the _p forms take it (BTN: a power of two
+ * 1..1024; OET: 1..1024) and, if stages != NULL, store the number of
+ * merge-split stages / rounds executed in *stages (host memory).
+ * Limits: n <= 32 * p (at most 32 keys per block) and n <= 16384; one CTA must
+ * hold the p blocks. Larger n gives ISORT_ERR_UNSUPPORTED.
+ * ------------------------------------------------------------------------- */
+ISORT_API isort_status isort_btn(uint32_t* keys, uint32_t* vals, size_t n, void* stream);
+ISORT_API isort_status isort_oet(uint32_t* keys, uint32_t* vals, size_t n, void* stream);
+ISORT_API isort_status isort_btn_p(uint32_t* keys, uint32_t* vals, size_t n, int p, uint64_t* stages, void* stream);
+ISORT_API isort_status isort_oet_p(uint32_t* keys, uint32_t* vals, size_t n, int p, uint64_t* stages, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Status mode and device-side checks.
+ * isort_set_sync(1) (default): calls wait for their work and return device
+ *   detected errors. isort_set_sync(0): calls return after enqueueing.
+ * isort_device_status: waits for `stream`, returns the first device-detected
+ *   error recorded by asynchronous calls on the current device since the last
+ *   clear (ISORT_OK if none), and clears it when clear != 0.
+ * isort_set_spin_limit: upper bound, in microseconds, of every device-side
+ *   wait (look-back, copy completion). A wait that runs out records
+ *   ISORT_ERR_TIMEOUT and the kernel returns. Default 2,000,000 (2 s).
+ * ------------------------------------------------------------------------- */
+ISORT_API isort_status isort_set_sync(int on);
+ISORT_API isort_status isort_device_status(int clear, void* stream);
+ISORT_API isort_status isort_set_spin_limit(uint64_t microseconds);
+
+/* ---------------------------------------------------------------------------
+ * Fault injection for tests: isort_debug_stall_tile(t) makes look-back tile t of
+ * the next radix round never publish its counts, so that its successors' waits
+ * run out (t < 0 disables). It only ever causes bounded waits.
+ * ------------------------------------------------------------------------- */
+ISORT_API isort_status isort_debug_stall_tile(int64_t tile);
+
+/* ---------------------------------------------------------------------------
+ * Introspection.
+ * isort_launch_count: number of kernels this library has launched so far in
+ *   this process.
+ * isort_profile_enable(1): record CUDA events around every kernel launch.
+ * isort_profile_read: waits for the recorded events, writes up to max entries
+ *   (one per kernel name: launches and total milliseconds) and clears the
+ *   record; returns the number of entries written.
+ * ------------------------------------------------------------------------- */
+ISORT_API uint64_t isort_launch_count(void);
+typedef struct {
+    char name[48];
+    uint64_t launches;
+    double total_ms;
+} isort_kernel_time;
+ISORT_API isort_status isort_profile_enable(int on);
+ISORT_API int isort_profile_read(isort_kernel_time* out, int max);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ISORT_H_ */

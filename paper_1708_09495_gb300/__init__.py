@@ -1,0 +1,236 @@
+"""GB300 integer sorting: Python binding of ``libisort.so``.
+
+The library implements, in hand-written CUDA for sm_103a, the count-sort
+rounds of LSD radix sort and the BTN / OET block networks of Gerbessiotis,
+"Integer sorting on multicores: some (experiments and) observations"
+(arXiv:1708.09495, Sections 2 and 3). This module only marshals arguments:
+every step of every sort runs in the library's kernels. PyTorch provides
+device memory and streams.
+
+Two layers:
+  * ``isort_*`` functions with the C ABI's names and arguments (raw pointers
+    as ints, sizes, a stream handle) — see ``include/isort.h``;
+  * tensor helpers (``radix``, ``radix_copy``, ``btn``, ``oet``, ``digit_hist``,
+    ``count_round``) that take torch tensors and raise ``IsortError``.
+
+There is no fallback: if the library is missing or fails to load, ``load()``
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libisort.so")
+
+STATUS = {
+    0: "ISORT_OK",
+    1: "ISORT_ERR_INVALID_ARG",
+    2: "ISORT_ERR_KEY_RANGE",
+    3: "ISORT_ERR_NO_MEMORY",
+    4: "ISORT_ERR_CUDA",
+    5: "ISORT_ERR_TIMEOUT",
+    6: "ISORT_ERR_UNSUPPORTED",
+}
+OK, INVALID_ARG, KEY_RANGE, NO_MEMORY, CUDA_ERROR, TIMEOUT, UNSUPPORTED = range(7)
+
+# Every symbol include/isort.h declares: (name, restype, argtypes).
+_vp, _sz, _i32, _u64, _i64 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint64, ctypes.c_int64
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
+
+
+SIGNATURES = [
+    ("isort_status_string", ctypes.c_char_p, [_i32]),
+    ("isort_radix", _i32, [_vp, _vp, _sz, _i32, _i32, _vp]),
+    ("isort_radix_u64", _i32, [_vp, _vp, _sz, _i32, _i32, _vp]),
+    ("isort_radix_copy", _i32, [_vp, _vp, _vp, _vp, _sz, _i32, _i32, _vp]),
+    ("isort_radix_copy_u64", _i32, [_vp, _vp, _vp, _vp, _sz, _i32, _i32, _vp]),
+    ("isort_digit_hist", _i32, [_vp, _i32, _sz, _i32, _i32, _vp, _vp]),
+    ("isort_count_round", _i32, [_vp, _vp, _vp, _vp, _sz, _i32, _i32, _vp]),
+    ("isort_count_round_u64", _i32, [_vp, _vp, _vp, _vp, _sz, _i32, _i32, _vp]),
+    ("isort_btn", _i32, [_vp, _vp, _sz, _vp]),
+    ("isort_oet", _i32, [_vp, _vp, _sz, _vp]),
+    ("isort_btn_p", _i32, [_vp, _vp, _sz, _i32, _vp, _vp]),
+    ("isort_oet_p", _i32, [_vp, _vp, _sz, _i32, _vp, _vp]),
+    ("isort_set_sync", _i32, [_i32]),
+    ("isort_device_status", _i32, [_i32, _vp]),
+    ("isort_set_spin_limit", _i32, [_u64]),
+    ("isort_debug_stall_tile", _i32, [_i64]),
+    ("isort_launch_count", _u64, []),
+    ("isort_profile_enable", _i32, [_i32]),
+    ("isort_profile_read", _i32, [ctypes.POINTER(KernelTime), _i32]),
+]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class IsortError(RuntimeError):
+    def __init__(self, code: int, where: str = ""):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)}" if where else STATUS.get(code, str(code)))
+
+
+def load(path: str | None = None):
+    """Loads the CUDA library (raises if it is missing: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(
+                    f"{p} is missing: build it first (python -c 'import __graft_entry__ as g; g.build()')")
+            lib = ctypes.CDLL(p)
+            for name, res, args in SIGNATURES:
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def lib():
+    return load()
+
+
+def __getattr__(name):
+    # isort_* raw entry points, resolved from the loaded library
+    if name.startswith("isort_"):
+        return getattr(load(), name)
+    raise AttributeError(name)
+
+
+# --------------------------------------------------------------------------- helpers
+
+
+def _stream(stream):
+    import torch
+
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("tensors must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(code: int, where: str):
+    if code != OK:
+        raise IsortError(code, where)
+
+
+def _key_width(t) -> int:
+    import torch
+
+    if t.dtype in (torch.uint32, torch.int32):
+        return 32
+    if t.dtype in (torch.uint64, torch.int64):
+        return 64
+    raise TypeError(f"keys must be 32- or 64-bit integers, got {t.dtype}")
+
+
+def radix(keys, vals=None, key_bits: int = 0, radix_bits: int = 8, stream=None):
+    """Stable in-place LSD radix sort of ``keys`` (uint32/uint64 bit patterns;
+    int32/int64 tensors are sorted as their unsigned bit patterns) with an
+    optional uint32 payload ``vals`` that moves with its key."""
+    w = _key_width(keys)
+    fn = load().isort_radix if w == 32 else load().isort_radix_u64
+    _check(fn(_ptr(keys), _ptr(vals), keys.numel(), key_bits, radix_bits, _stream(stream)), "isort_radix")
+    return keys, vals
+
+
+def radix_copy(keys_in, vals_in, keys_out, vals_out, key_bits: int = 0, radix_bits: int = 8, stream=None):
+    """Stable out-of-place LSD radix sort: inputs read, result in the outputs."""
+    w = _key_width(keys_in)
+    fn = load().isort_radix_copy if w == 32 else load().isort_radix_copy_u64
+    _check(fn(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out), _ptr(vals_out), keys_in.numel(), key_bits, radix_bits,
+              _stream(stream)), "isort_radix_copy")
+    return keys_out, vals_out
+
+
+def digit_hist(keys, key_bits: int = 0, radix_bits: int = 8, stream=None):
+    """Per-round digit counts, shape (rounds, 2^radix_bits), as a uint32 tensor."""
+    import torch
+
+    w = _key_width(keys)
+    kb = key_bits or w
+    rounds = -(-kb // radix_bits)
+    hist = torch.empty((rounds, 1 << radix_bits), dtype=torch.uint32, device=keys.device)
+    _check(load().isort_digit_hist(_ptr(keys), w, keys.numel(), key_bits, radix_bits, _ptr(hist), _stream(stream)),
+           "isort_digit_hist")
+    return hist
+
+
+def count_round(keys_in, vals_in, shift: int, width: int, stream=None):
+    """One stable count-sort round on digit (key >> shift) & (2^width - 1)."""
+    import torch
+
+    w = _key_width(keys_in)
+    ko = torch.empty_like(keys_in)
+    vo = None if vals_in is None else torch.empty_like(vals_in)
+    fn = load().isort_count_round if w == 32 else load().isort_count_round_u64
+    _check(fn(_ptr(keys_in), _ptr(vals_in), _ptr(ko), _ptr(vo), keys_in.numel(), shift, width, _stream(stream)),
+           "isort_count_round")
+    return ko, vo
+
+
+def btn(keys, vals=None, p: int | None = None, stream=None):
+    """In-place BTN sort (uint32 keys). With ``p`` given, returns the number
+    of merge-split stages executed as well."""
+    if p is None:
+        _check(load().isort_btn(_ptr(keys), _ptr(vals), keys.numel(), _stream(stream)), "isort_btn")
+        return keys, vals
+    st = ctypes.c_uint64(0)
+    _check(load().isort_btn_p(_ptr(keys), _ptr(vals), keys.numel(), p, ctypes.byref(st), _stream(stream)),
+           "isort_btn_p")
+    return keys, vals, int(st.value)
+
+
+def oet(keys, vals=None, p: int | None = None, stream=None):
+    """In-place OET sort (uint32 keys). With ``p`` given, also returns rounds."""
+    if p is None:
+        _check(load().isort_oet(_ptr(keys), _ptr(vals), keys.numel(), _stream(stream)), "isort_oet")
+        return keys, vals
+    st = ctypes.c_uint64(0)
+    _check(load().isort_oet_p(_ptr(keys), _ptr(vals), keys.numel(), p, ctypes.byref(st), _stream(stream)),
+           "isort_oet_p")
+    return keys, vals, int(st.value)
+
+
+def set_sync(on: bool):
+    _check(load().isort_set_sync(1 if on else 0), "isort_set_sync")
+
+
+def device_status(clear: bool = True, stream=None) -> int:
+    return int(load().isort_device_status(1 if clear else 0, _stream(stream)))
+
+
+def set_spin_limit(microseconds: int):
+    _check(load().isort_set_spin_limit(int(microseconds)), "isort_set_spin_limit")
+
+
+def launch_count() -> int:
+    return int(load().isort_launch_count())
+
+
+def profile_enable(on: bool):
+    _check(load().isort_profile_enable(1 if on else 0), "isort_profile_enable")
+
+
+def profile_read(max_entries: int = 64):
+    """{kernel name: (launches, total_ms)} recorded since the last read."""
+    buf = (KernelTime * max_entries)()
+    k = load().isort_profile_read(buf, max_entries)
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(k)}

@@ -1,0 +1,53 @@
+// Host-side runtime shared by the entry points: the per-device scratch pool,
+// the status mode, launch accounting and optional per-kernel event timing.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/isort.h"
+
+namespace isort {
+
+// Scratch memory, stream-ordered, from a pool owned by the library.
+isort_status scratch_alloc(void** p, size_t bytes, cudaStream_t s);
+void scratch_free(void* p, cudaStream_t s);
+
+int sm_count();                 // SMs of the current device
+size_t max_smem_optin();        // opt-in dynamic shared memory per block
+bool sync_mode();
+uint64_t spin_limit_ns();
+int64_t take_stall_tile();      // consumes the injected stall (-1 if none)
+
+// Finishes a call whose kernels recorded device errors into d_status:
+// in synchronous mode waits for `s` and maps the bits to a status; in
+// asynchronous mode folds them into the device's sticky status word.
+isort_status finish_status(const uint32_t* d_status, cudaStream_t s);
+
+isort_status from_cuda(cudaError_t e);
+
+// True when p points to host memory (pinned or pageable).
+bool is_host_pointer(const void* p);
+
+// Launch accounting / profiling: construct before a launch, destroy after.
+class LaunchScope {
+   public:
+    LaunchScope(const char* name, cudaStream_t s);
+    ~LaunchScope();
+
+   private:
+    const char* name_;
+    cudaStream_t s_;
+    cudaEvent_t e0_ = nullptr;
+};
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace isort
+
+#define ISORT_TRY_CUDA(expr)                                 \
+    do {                                                     \
+        cudaError_t e_ = (expr);                             \
+        if (e_ != cudaSuccess) return ::isort::from_cuda(e_); \
+    } while (0)
