@@ -113,6 +113,18 @@ def make_inputs():
     return workloads.large_uniform(N, 32, SEED, payload=True)
 
 
+def configure(args):
+    """--log2n / --radix-bits select a smaller or differently-digited case of
+    the same workload (profiling); the defaults are the benchmark."""
+    global N, RADIX_BITS, ROUNDS, BYTES_PER_KEY, WORKLOAD
+    N = 1 << args.log2n
+    RADIX_BITS = args.radix_bits
+    ROUNDS = -(-KEY_BITS // RADIX_BITS)
+    BYTES_PER_KEY = 4 + ROUNDS * 2 * (4 + 4)
+    WORKLOAD = (f"stable LSD radix sort, u32 keys uniform on [0,2^32) (seed 2) + u32 payload = index, "
+                f"n = 2^{args.log2n}, radix 2^{RADIX_BITS} ({ROUNDS} rounds), out of place")
+
+
 def cpu_baseline_oracle(keys, vals, sample_n: int, reps: int):
     """The serial C oracle (1 core) on the first sample_n keys; Gkeys/s."""
     import oracle
@@ -133,7 +145,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     keys, vals = make_inputs()
-    sample_n = 1 << 23
+    sample_n = min(N, 1 << 23)
     import oracle
 
     k, v = keys[:sample_n].copy(), vals[:sample_n].copy()
@@ -190,7 +202,7 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
     # correctness spot check of the bench's own output (sorted + stable)
-    sk = ko[:: N // 4096].cpu().numpy().view(np.uint32)
+    sk = ko[:: max(1, N // 4096)].cpu().numpy().view(np.uint32)
     if not np.all(sk[1:] >= sk[:-1]):
         raise RuntimeError("bench output not sorted")
 
@@ -260,7 +272,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        v, t, times = cpu_baseline_oracle(keys, vals, 1 << 24, 3)
+        v, t, times = cpu_baseline_oracle(keys, vals, min(N, 1 << 24), 3)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "first 2^24 keys (+payload) of the workload, serial C oracle, median of 3 runs"}
 
@@ -297,7 +309,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--log2n", type=int, default=28)
+    ap.add_argument("--radix-bits", type=int, default=8)
     args = ap.parse_args()
+    configure(args)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":

@@ -123,13 +123,34 @@ ISORT_API isort_status isort_count_round_u64(const uint64_t* keys_in, const uint
  * isort_btn / isort_oet choose p; the _p forms take it (BTN: a power of two
  * 1..1024; OET: 1..1024) and, if stages != NULL, store the number of
  * merge-split stages / rounds executed in *stages (host memory).
- * Limits: n <= 32 * p (at most 32 keys per block) and n <= 16384; one CTA must
- * hold the p blocks. Larger n gives ISORT_ERR_UNSUPPORTED.
+ * Limits: one CTA holds the p blocks: n <= 16384, at most 32 keys per block
+ * (n <= 32 * p), and at most 16 keys per block when p > 512. Other sizes give
+ * ISORT_ERR_UNSUPPORTED.
  * ------------------------------------------------------------------------- */
 ISORT_API isort_status isort_btn(uint32_t* keys, uint32_t* vals, size_t n, void* stream);
 ISORT_API isort_status isort_oet(uint32_t* keys, uint32_t* vals, size_t n, void* stream);
 ISORT_API isort_status isort_btn_p(uint32_t* keys, uint32_t* vals, size_t n, int p, uint64_t* stages, void* stream);
 ISORT_API isort_status isort_oet_p(uint32_t* keys, uint32_t* vals, size_t n, int p, uint64_t* stages, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched segmented sort: segment s is keys[seg_offsets[s] .. seg_offsets[s+1])
+ * (with the same range of vals); every segment is sorted stably and in place,
+ * independently of the others. One launch sequence, captured in a CUDA graph,
+ * serves all segments; each segment is routed on the device by its length to
+ * OET (Section 2; <= 32 keys, one warp), BTN (Section 2, eq. Tb; <= 256 keys in
+ * one warp, <= 4096 keys in one CTA) or count-sort rounds of 8-bit digits
+ * (Section 3, eq. Ts) run entirely on chip by a cluster of 1, 2, 4 or 8 CTAs
+ * (<= 65,536 keys). Longer segments use isort_radix's rounds, one segment at a
+ * time; in the asynchronous status mode or while `stream` is being captured
+ * they are not supported (ISORT_ERR_UNSUPPORTED recorded).
+ * keys, vals (may be NULL) and seg_offsets (nseg + 1 uint64, non-decreasing)
+ * are device memory. key_bits as for isort_radix; a segment holding a key
+ * >= 2^key_bits is left unchanged and ISORT_ERR_KEY_RANGE is returned; other
+ * segments are still sorted. Decreasing offsets: ISORT_ERR_INVALID_ARG (those
+ * segments are skipped). nseg < 2^31.
+ * ------------------------------------------------------------------------- */
+ISORT_API isort_status isort_segmented(uint32_t* keys, uint32_t* vals, const uint64_t* seg_offsets, size_t nseg,
+                                       int key_bits, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Status mode and device-side checks.

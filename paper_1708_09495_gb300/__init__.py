@@ -57,6 +57,7 @@ SIGNATURES = [
     ("isort_oet", _i32, [_vp, _vp, _sz, _vp]),
     ("isort_btn_p", _i32, [_vp, _vp, _sz, _i32, _vp, _vp]),
     ("isort_oet_p", _i32, [_vp, _vp, _sz, _i32, _vp, _vp]),
+    ("isort_segmented", _i32, [_vp, _vp, _vp, _sz, _i32, _vp]),
     ("isort_set_sync", _i32, [_i32]),
     ("isort_device_status", _i32, [_i32, _vp]),
     ("isort_set_spin_limit", _i32, [_u64]),
@@ -207,6 +208,16 @@ def oet(keys, vals=None, p: int | None = None, stream=None):
     _check(load().isort_oet_p(_ptr(keys), _ptr(vals), keys.numel(), p, ctypes.byref(st), _stream(stream)),
            "isort_oet_p")
     return keys, vals, int(st.value)
+
+
+def segmented(keys, vals, offsets, key_bits: int = 0, stream=None):
+    """Sorts each CSR segment [offsets[s], offsets[s+1]) of keys (and vals) in
+    place; offsets is a uint64/int64 device tensor of nseg + 1 entries."""
+    if offsets.element_size() != 8:
+        raise TypeError("offsets must be 64-bit")
+    _check(load().isort_segmented(_ptr(keys), _ptr(vals), _ptr(offsets), offsets.numel() - 1, key_bits,
+                                  _stream(stream)), "isort_segmented")
+    return keys, vals
 
 
 def set_sync(on: bool):

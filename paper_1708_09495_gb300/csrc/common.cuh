@@ -13,6 +13,8 @@ enum : uint32_t {
     kStatKeyRange = 1u << 0,  // a key >= 2^key_bits was seen
     kStatTimeout = 1u << 1,   // a bounded wait ran out
     kStatBounds = 1u << 2,    // an output index fell outside [0, n) (never expected)
+    kStatBadOffsets = 1u << 3,  // segment offsets decrease
+    kStatUnsupported = 1u << 4, // a case the asynchronous path cannot take
 };
 
 constexpr unsigned kFullMask = 0xffffffffu;

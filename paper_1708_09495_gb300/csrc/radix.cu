@@ -19,12 +19,50 @@
 //                 digit in shared memory and write them out in runs.
 // So each round costs one read and one write of the keys (and payloads).
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "common.cuh"
 #include "runtime.h"
 
 namespace isort {
+
+// Tunables of the radix path. Defaults are the measured best on GB300; the
+// environment variable ISORT_TUNE ("key=value,...") overrides them.
+struct Tune {
+    int hist_agg = 0;     // 1: match-any aggregation in the digit histogram
+    int rank_mode = 1;    // 0: match-any ranking, 1: per-bit ballot ranking
+    int shape_small = 4;  // launch shape for digits of <= 8 bits
+    int shape_large = 1;  // launch shape for wider digits
+};
+
+static Tune load_tune() {
+    Tune t;
+    const char* e = getenv("ISORT_TUNE");
+    if (!e) return t;
+    char key[32];
+    int val;
+    const char* p = e;
+    while (*p) {
+        int used = 0;
+        if (sscanf(p, "%31[a-z_0-9]=%d%n", key, &val, &used) != 2 || used == 0) break;
+        if (!strcmp(key, "hist_agg")) t.hist_agg = val;
+        else if (!strcmp(key, "rank")) t.rank_mode = val;
+        else if (!strcmp(key, "shape8")) t.shape_small = val;
+        else if (!strcmp(key, "shape11")) t.shape_large = val;
+        p += used;
+        if (*p == ',') ++p;
+    }
+    if (t.shape_small < 0 || t.shape_small >= 6) t.shape_small = 4;
+    if (t.shape_large < 0 || t.shape_large >= 6) t.shape_large = 1;
+    return t;
+}
+
+const Tune& tune() {
+    static const Tune t = load_tune();
+    return t;
+}
 
 // ----------------------------------------------------------------------------
 // Digit histogram of all rounds (one read).
@@ -72,7 +110,7 @@ __device__ __forceinline__ void hist_count_key_warp(K k, uint32_t* s_hist, int s
     }
 }
 
-template <typename K>
+template <typename K, bool AGG>
 __global__ void __launch_bounds__(kHistThreads) k_digit_hist(HistArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int bins = 1 << a.radix_bits;
@@ -130,14 +168,20 @@ __global__ void __launch_bounds__(kHistThreads) k_digit_hist(HistArgs a) {
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     acc |= (K)w[e];
-                    hist_count_key_warp<K>((K)w[e], s_hist, a.shift0, a.rounds, a.radix_bits, a.key_bits, bins);
+                    if constexpr (AGG)
+                        hist_count_key_warp<K>((K)w[e], s_hist, a.shift0, a.rounds, a.radix_bits, a.key_bits, bins);
+                    else
+                        hist_count_key<K>((K)w[e], s_hist, a.shift0, a.rounds, a.radix_bits, a.key_bits, bins);
                 }
             } else {
                 const K w[2] = {((K)v.y << 32) | v.x, ((K)v.w << 32) | v.z};
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
                     acc |= w[e];
-                    hist_count_key_warp<K>(w[e], s_hist, a.shift0, a.rounds, a.radix_bits, a.key_bits, bins);
+                    if constexpr (AGG)
+                        hist_count_key_warp<K>(w[e], s_hist, a.shift0, a.rounds, a.radix_bits, a.key_bits, bins);
+                    else
+                        hist_count_key<K>(w[e], s_hist, a.shift0, a.rounds, a.radix_bits, a.key_bits, bins);
                 }
             }
         }
@@ -232,7 +276,8 @@ struct PassArgs {
     uint32_t* vals_out;
     uint32_t n;
     int shift;
-    int bins;                  // 2^width of this round's digit
+    int width;                 // digit bits of this round
+    int bins;                  // 2^width
     const uint32_t* bin_off;   // [bins] exclusive global offsets
     uint32_t* lookback;        // [num_tiles][bins]
     uint32_t* tile_counter;
@@ -296,8 +341,27 @@ struct OnesweepCfg {
     }
 };
 
-template <typename K, bool VALS, int THREADS, int ITEMS>
-__global__ void __launch_bounds__(THREADS) k_onesweep(PassArgs a) {
+// Peers of this lane: the lanes of the warp holding a valid key with the
+// same digit. RANK 0 uses one match-any vote; RANK 1 intersects one ballot per
+// digit bit (no match unit involved).
+template <int RANK>
+__device__ __forceinline__ uint32_t warp_peers(uint32_t d, bool valid, int width) {
+    if constexpr (RANK == 0) {
+        return __match_any_sync(kFullMask, valid ? d : 0xffffffffu);
+    } else {
+        uint32_t peers = __ballot_sync(kFullMask, valid);
+#pragma unroll 4
+        for (int b = 0; b < width; ++b) {
+            const bool bit = (d >> b) & 1u;
+            const uint32_t bal = __ballot_sync(kFullMask, bit);
+            peers &= bit ? bal : ~bal;
+        }
+        return peers;
+    }
+}
+
+template <typename K, bool VALS, int THREADS, int ITEMS, int RANK>
+__global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREADS) : 1) k_onesweep(PassArgs a) {
     using Cfg = OnesweepCfg<K, VALS, THREADS, ITEMS>;
     constexpr int WARPS = Cfg::kWarps;
     constexpr int TILE = Cfg::kTile;
@@ -344,7 +408,7 @@ __global__ void __launch_bounds__(THREADS) k_onesweep(PassArgs a) {
 
     uint32_t tile = s_next_tile;
     if (tid == 0 && tile < a.num_tiles && full_bulk_tile(tile)) issue_tile(tile, 0);
-    uint32_t uses[2] = {0u, 0u};
+    uint32_t phase = 0u;  // bit b: parity of the next completion of buffer b's barrier
     int b = 0;
 
     while (tile < a.num_tiles) {
@@ -363,8 +427,8 @@ __global__ void __launch_bounds__(THREADS) k_onesweep(PassArgs a) {
         const uint32_t tile_n = min((uint32_t)TILE, a.n - tile_base);
         bool ok = true;
         if (full_bulk_tile(tile)) {
-            ok = mbar_wait_bounded(&bars[b], uses[b] & 1u, a.limit_ns);
-            uses[b]++;
+            ok = mbar_wait_bounded(&bars[b], (phase >> b) & 1u, a.limit_ns);
+            phase ^= 1u << b;
         } else {
             for (uint32_t j = tid; j < tile_n; j += THREADS) {
                 s_keys[j] = keys_in[tile_base + j];
@@ -378,7 +442,7 @@ __global__ void __launch_bounds__(THREADS) k_onesweep(PassArgs a) {
             // copy this CTA issued into the other buffer, and stop
             if (tid == 0) set_status(a.status, kStatTimeout);
             if (next_tile < a.num_tiles && full_bulk_tile(next_tile))
-                mbar_wait_bounded(&bars[b ^ 1], uses[b ^ 1] & 1u, a.limit_ns);
+                mbar_wait_bounded(&bars[b ^ 1], (phase >> (b ^ 1)) & 1u, a.limit_ns);
             return;
         }
         const bool stalled = (long long)tile == a.stall_tile;  // fault injection: never publish
@@ -395,8 +459,8 @@ __global__ void __launch_bounds__(THREADS) k_onesweep(PassArgs a) {
                 const K k = valid ? s_keys[j] : (K)0;
                 kreg[i] = k;
                 if constexpr (VALS) vreg[i] = valid ? s_vals[j] : 0u;
-                const uint32_t d = valid ? ((uint32_t)(k >> a.shift) & dmask) : 0xffffffffu;
-                const uint32_t peers = __match_any_sync(kFullMask, d);
+                const uint32_t d = (uint32_t)(k >> a.shift) & dmask;
+                const uint32_t peers = warp_peers<RANK>(d, valid, a.width);
                 const uint32_t below = (uint32_t)__popc(peers & lanemask_lt());
                 const uint32_t c = valid ? (uint32_t)s_cnt[warp * bins + d] : 0u;
                 rank[i] = c + below;
@@ -425,7 +489,12 @@ __global__ void __launch_bounds__(THREADS) k_onesweep(PassArgs a) {
             __syncthreads();
             block_exclusive_scan<THREADS>(s_bin_start, bins, s_warp_scan);
 
-            // ---- decoupled look-back: sum earlier tiles' counts per digit
+            // ---- decoupled look-back: sum earlier tiles' counts per digit.
+            //      A window of kWin predecessors is read at once (the reads are
+            //      independent), then consumed nearest first until a tile with
+            //      an inclusive count is met; a predecessor that has published
+            //      nothing yet is re-read after a short sleep (bounded).
+            constexpr int kWin = 16;
             int lfail = 0;
             for (int d = tid; d < bins; d += THREADS) {
                 const uint32_t total = s_delta[d];
@@ -434,19 +503,30 @@ __global__ void __launch_bounds__(THREADS) k_onesweep(PassArgs a) {
                     long long t = (long long)tile - 1;
                     uint64_t t0 = 0;
                     uint32_t spins = 0;
-                    while (t >= 0) {
-                        const uint32_t w = ld_relaxed(&a.lookback[(size_t)t * bins + d]);
-                        const uint32_t flag = w & ~kCountMask;
-                        if (flag == 0) {
+                    bool done = false;
+                    while (!done && t >= 0) {
+                        uint32_t w[kWin];
+#pragma unroll
+                        for (int q = 0; q < kWin; ++q)
+                            w[q] = t - q >= 0 ? ld_relaxed(&a.lookback[(size_t)(t - q) * bins + d]) : kFlagInc;
+                        int used = 0;
+                        bool stall = false;
+#pragma unroll
+                        for (int q = 0; q < kWin; ++q) {
+                            if (done || stall) continue;
+                            const uint32_t flag = w[q] & ~kCountMask;
+                            if (flag == 0) { stall = true; continue; }
+                            excl += w[q] & kCountMask;
+                            ++used;
+                            if (flag == kFlagInc) done = true;
+                        }
+                        t -= used;
+                        if (stall && !done) {
                             if (t0 == 0) t0 = global_timer_ns();
                             else if (global_timer_ns() - t0 > a.limit_ns) { lfail = 1; break; }
                             if ((++spins & 31u) == 0 && ld_relaxed(a.status) != 0) { lfail = 1; break; }
-                            __nanosleep(32);
-                            continue;
+                            __nanosleep(20);
                         }
-                        excl += w & kCountMask;
-                        if (flag == kFlagInc) break;
-                        --t;
                     }
                     if (lfail) set_status(a.status, kStatTimeout);
                     __threadfence();
@@ -498,16 +578,16 @@ __global__ void __launch_bounds__(THREADS) k_onesweep(PassArgs a) {
 // ----------------------------------------------------------------------------
 namespace {
 
-// Launch shape of one round for a digit of `bins` values.
-enum class Shape { T512x8, T256x16 };
+// Launch shapes of a round (threads x keys per thread).
+constexpr int kShapeThreads[] = {512, 256, 256, 128, 512, 1024};
+constexpr int kShapeItems[] = {8, 16, 8, 16, 16, 8};
 
-Shape pick_shape(int bins) { return bins <= 256 ? Shape::T512x8 : Shape::T256x16; }
-int shape_tile(Shape s) { return s == Shape::T512x8 ? 4096 : 4096; }
+int shape_tile(int sh) { return kShapeThreads[sh] * kShapeItems[sh]; }
 
-template <typename K, bool VALS, int THREADS, int ITEMS>
+template <typename K, bool VALS, int THREADS, int ITEMS, int RANK>
 isort_status launch_round(PassArgs a, cudaStream_t s) {
     using Cfg = OnesweepCfg<K, VALS, THREADS, ITEMS>;
-    auto kern = k_onesweep<K, VALS, THREADS, ITEMS>;
+    auto kern = k_onesweep<K, VALS, THREADS, ITEMS, RANK>;
     const size_t smem = Cfg::smem_bytes(a.bins);
     if (smem > max_smem_optin()) return ISORT_ERR_UNSUPPORTED;
     ISORT_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -520,11 +600,23 @@ isort_status launch_round(PassArgs a, cudaStream_t s) {
     return from_cuda(cudaGetLastError());
 }
 
+template <typename K, bool VALS, int RANK>
+isort_status launch_round_shape(int sh, PassArgs a, cudaStream_t s) {
+    switch (sh) {
+        case 0: return launch_round<K, VALS, 512, 8, RANK>(a, s);
+        case 1: return launch_round<K, VALS, 256, 16, RANK>(a, s);
+        case 2: return launch_round<K, VALS, 256, 8, RANK>(a, s);
+        case 3: return launch_round<K, VALS, 128, 16, RANK>(a, s);
+        case 4: return launch_round<K, VALS, 512, 16, RANK>(a, s);
+        default: return launch_round<K, VALS, 1024, 8, RANK>(a, s);
+    }
+}
+
 template <typename K>
-isort_status launch_round_dispatch(Shape sh, bool vals, PassArgs a, cudaStream_t s) {
-    if (sh == Shape::T512x8)
-        return vals ? launch_round<K, true, 512, 8>(a, s) : launch_round<K, false, 512, 8>(a, s);
-    return vals ? launch_round<K, true, 256, 16>(a, s) : launch_round<K, false, 256, 16>(a, s);
+isort_status launch_round_dispatch(int sh, bool vals, PassArgs a, cudaStream_t s) {
+    const int rank = tune().rank_mode;
+    if (vals) return rank ? launch_round_shape<K, true, 1>(sh, a, s) : launch_round_shape<K, true, 0>(sh, a, s);
+    return rank ? launch_round_shape<K, false, 1>(sh, a, s) : launch_round_shape<K, false, 0>(sh, a, s);
 }
 
 template <typename K>
@@ -545,7 +637,7 @@ isort_status launch_hist(const K* keys, size_t n, int shift0, int rb, int key_bi
     const int bins = 1 << rb;
     const size_t smem = kHistStages * kHistChunkBytes + align_up((size_t)rounds * bins * 4, 8) + kHistStages * 8;
     if (smem > max_smem_optin()) return ISORT_ERR_UNSUPPORTED;
-    auto kern = k_digit_hist<K>;
+    auto kern = tune().hist_agg ? k_digit_hist<K, true> : k_digit_hist<K, false>;
     ISORT_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     ISORT_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kHistThreads, smem));
@@ -615,7 +707,7 @@ isort_status radix_device(const K* kin, const uint32_t* vin, K* kout, uint32_t* 
     if (rb > 12) return ISORT_ERR_UNSUPPORTED;
     const bool vals = vin != nullptr;
     const bool inplace = (const void*)kin == (const void*)kout;
-    const Shape sh = pick_shape(bins);
+    const int sh = bins <= 256 ? tune().shape_small : tune().shape_large;
     const uint32_t tile = (uint32_t)shape_tile(sh);
     const uint32_t num_tiles = (uint32_t)((n + tile - 1) / tile);
 
@@ -683,6 +775,7 @@ isort_status radix_device(const K* kin, const uint32_t* vin, K* kout, uint32_t* 
         a.vals_out = dv;
         a.n = (uint32_t)n;
         a.shift = shift;
+        a.width = width;
         a.bins = 1 << width;
         a.bin_off = c.offs + (size_t)d * bins;
         a.lookback = c.lookback + (size_t)d * num_tiles * bins;
@@ -783,7 +876,7 @@ isort_status count_round_entry(const K* kin, const uint32_t* vin, K* kout, uint3
         return ISORT_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int bins = 1 << width;
-    const Shape sh = pick_shape(bins);
+    const int sh = bins <= 256 ? tune().shape_small : tune().shape_large;
     const uint32_t tile = (uint32_t)shape_tile(sh);
     const uint32_t num_tiles = (uint32_t)((n + tile - 1) / tile);
     Ctl probe = layout_ctl(nullptr, 1, bins, num_tiles, true);
@@ -809,6 +902,7 @@ isort_status count_round_entry(const K* kin, const uint32_t* vin, K* kout, uint3
     a.vals_out = vout;
     a.n = (uint32_t)n;
     a.shift = shift;
+    a.width = width;
     a.bins = bins;
     a.bin_off = c.offs;
     a.lookback = c.lookback;

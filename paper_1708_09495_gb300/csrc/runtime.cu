@@ -121,6 +121,8 @@ int64_t take_stall_tile() { return g_stall.exchange(-1); }
 
 static isort_status map_bits(uint32_t v) {
     if (v & kStatTimeout) return ISORT_ERR_TIMEOUT;
+    if (v & kStatBadOffsets) return ISORT_ERR_INVALID_ARG;
+    if (v & kStatUnsupported) return ISORT_ERR_UNSUPPORTED;
     if (v & kStatKeyRange) return ISORT_ERR_KEY_RANGE;
     if (v & kStatBounds) return ISORT_ERR_CUDA;
     return ISORT_OK;
@@ -155,9 +157,14 @@ bool is_host_pointer(const void* p) {
     return a.type == cudaMemoryTypeUnregistered || a.type == cudaMemoryTypeHost;
 }
 
-LaunchScope::LaunchScope(const char* name, cudaStream_t s) : name_(name), s_(s) {
-    g_launches.fetch_add(1);
-    if (g_profile.load()) {
+thread_local int t_capturing = 0;
+
+CaptureScope::CaptureScope() { ++t_capturing; }
+CaptureScope::~CaptureScope() { --t_capturing; }
+
+LaunchScope::LaunchScope(const char* name, cudaStream_t s, bool count) : name_(name), s_(s) {
+    if (count) g_launches.fetch_add(1);
+    if (g_profile.load() && t_capturing == 0) {
         if (cudaEventCreate(&e0_) == cudaSuccess) cudaEventRecord(e0_, s_);
         else e0_ = nullptr;
     }

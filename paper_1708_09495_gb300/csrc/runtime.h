@@ -31,15 +31,24 @@ isort_status from_cuda(cudaError_t e);
 bool is_host_pointer(const void* p);
 
 // Launch accounting / profiling: construct before a launch, destroy after.
+// count = false times a launch (e.g. of a graph) without counting it as a
+// kernel. While a CaptureScope is alive on this thread, launches are counted
+// but not timed (events cannot bracket captured work).
 class LaunchScope {
    public:
-    LaunchScope(const char* name, cudaStream_t s);
+    LaunchScope(const char* name, cudaStream_t s, bool count = true);
     ~LaunchScope();
 
    private:
     const char* name_;
     cudaStream_t s_;
     cudaEvent_t e0_ = nullptr;
+};
+
+class CaptureScope {
+   public:
+    CaptureScope();
+    ~CaptureScope();
 };
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }

@@ -2,185 +2,30 @@
 // arXiv:1708.09495, Section 2; Section 3 "Bitonic Sort" eq. Tb and "Odd-even
 // transposition sort" eq. To).
 //
-// p "processors" are p threads of one CTA. Thread t holds block t: B
-// consecutive items of the (padded) input in registers, as 64-bit composites
-// (key << 32 | original index). Comparing composites compares (key, index), so
-// the networks' result is the unique stable order even though merge-split
-// networks are not stable by themselves.
-//
-// Merge-split of two ascending blocks X (this thread) and Y (partner) without
-// a serial merge: Z[i] = min(X[i], Y[B-1-i]) is exactly the B smallest items of
-// X u Y and forms a bitonic sequence (the first half-cleaner of the bitonic
-// sequence X ++ reverse(Y)); max() gives the B largest. A log2(B)-stage
-// bitonic merge in registers then sorts Z. The partner's items are fetched one
-// at a time (warp shuffle when the partner is in the same warp, shared memory
-// otherwise), so a thread never holds two blocks.
+// p "processors" are p threads of one CTA; the device code is in net.cuh.
 #include <algorithm>
 
 #include "common.cuh"
+#include "net.cuh"
 #include "runtime.h"
 
 namespace isort {
 namespace {
 
-constexpr uint64_t kPadHi = 0xFFFFFFFFull << 32;
-
-__device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
-__device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a < b ? b : a; }
-
+// BTN: one CTA, p (a power of two) threads hold the blocks.
 template <int B>
-__device__ __forceinline__ void cswap(uint64_t (&x)[B], int i, int l, bool asc) {
-    const uint64_t a = x[i], b = x[l];
-    const bool sw = asc ? (a > b) : (a < b);
-    x[i] = sw ? b : a;
-    x[l] = sw ? a : b;
-}
-
-// Local sort of a block (a register bitonic sorting network, ascending).
-template <int B>
-__device__ __forceinline__ void local_sort(uint64_t (&x)[B]) {
-#pragma unroll
-    for (int k = 2; k <= B; k <<= 1)
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1)
-#pragma unroll
-            for (int i = 0; i < B; ++i) {
-                const int l = i ^ j;
-                if (l > i) cswap<B>(x, i, l, (i & k) == 0);
-            }
-}
-
-// Sorts a bitonic block ascending.
-template <int B>
-__device__ __forceinline__ void bitonic_merge(uint64_t (&x)[B]) {
-#pragma unroll
-    for (int j = B >> 1; j > 0; j >>= 1)
-#pragma unroll
-        for (int i = 0; i < B; ++i) {
-            const int l = i ^ j;
-            if (l > i) cswap<B>(x, i, l, true);
-        }
-}
-
-template <int B>
-__device__ __forceinline__ void load_block(uint64_t (&x)[B], const uint32_t* keys, uint32_t n, int t) {
-#pragma unroll
-    for (int i = 0; i < B; ++i) {
-        const uint32_t g = (uint32_t)t * B + i;
-        x[i] = g < n ? (((uint64_t)keys[g] << 32) | g) : (kPadHi | g);
-    }
-}
-
-// Writes the first n items of the sorted sequence; payloads are gathered by
-// original index. All reads of the inputs finish before any write (in place).
-template <int B>
-__device__ __forceinline__ void store_block(const uint64_t (&x)[B], uint32_t* keys, uint32_t* vals, uint32_t n,
-                                            int t, bool active) {
-    uint32_t v[B];
-    if (vals && active) {
-#pragma unroll
-        for (int i = 0; i < B; ++i) {
-            const uint32_t g = (uint32_t)t * B + i;
-            v[i] = g < n ? vals[(uint32_t)x[i]] : 0u;
-        }
-    }
-    __syncthreads();
-    if (!active) return;
-#pragma unroll
-    for (int i = 0; i < B; ++i) {
-        const uint32_t g = (uint32_t)t * B + i;
-        if (g < n) {
-            keys[g] = (uint32_t)(x[i] >> 32);
-            if (vals) vals[g] = v[i];
-        }
-    }
-}
-
-// Half-cleaner against the partner lane (t ^ j) of the same warp. Slots i and
-// B-1-i are exchanged together so that only original values are sent.
-template <int B>
-__device__ __forceinline__ void merge_split_shfl(uint64_t (&x)[B], int j, bool keep_small) {
-    if constexpr (B == 1) {
-        const uint64_t y = __shfl_xor_sync(kFullMask, x[0], j);
-        x[0] = keep_small ? umin64(x[0], y) : umax64(x[0], y);
-    } else {
-#pragma unroll
-        for (int i = 0; i < B / 2; ++i) {
-            const uint64_t a = x[i], b = x[B - 1 - i];
-            const uint64_t ya = __shfl_xor_sync(kFullMask, b, j);  // partner's item B-1-i
-            const uint64_t yb = __shfl_xor_sync(kFullMask, a, j);  // partner's item i
-            x[i] = keep_small ? umin64(a, ya) : umax64(a, ya);
-            x[B - 1 - i] = keep_small ? umin64(b, yb) : umax64(b, yb);
-        }
-    }
-}
-
-// Half-cleaner against block `partner` through shared memory.
-template <int B>
-__device__ __forceinline__ void merge_split_smem(uint64_t (&x)[B], uint64_t* s_x, int P, int t, int partner,
-                                                 bool exchange, bool keep_small) {
-#pragma unroll
-    for (int i = 0; i < B; ++i) s_x[i * P + t] = x[i];
-    __syncthreads();
-    if (exchange) {
-#pragma unroll
-        for (int i = 0; i < B; ++i) {
-            const uint64_t y = s_x[(B - 1 - i) * P + partner];
-            x[i] = keep_small ? umin64(x[i], y) : umax64(x[i], y);
-        }
-    }
-    __syncthreads();
-}
-
-// BTN: p (a power of two) threads; lg p (lg p + 1)/2 merge-split stages.
-template <int B>
-__global__ void k_btn(uint32_t* keys, uint32_t* vals, uint32_t n, int p, unsigned long long* stage_ctr) {
+__global__ void __launch_bounds__(B <= 16 ? 1024 : 512)
+    k_btn(uint32_t* keys, uint32_t* vals, uint32_t n, int p, unsigned long long* stage_ctr) {
     extern __shared__ __align__(16) uint64_t s_x[];  // [B][blockDim] when a stage crosses warps
-    const int t = threadIdx.x;
-    const int P = blockDim.x;
-    const bool active = t < p;
-    uint64_t x[B];
-    load_block<B>(x, keys, n, t);  // threads >= p hold pads only
-    local_sort<B>(x);
-    for (int k = 2; k <= p; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            const int partner = t ^ j;
-            const bool asc = (t & k) == 0;
-            const bool lower = t < partner;
-            const bool keep_small = lower == asc;
-            if (j < 32) {
-                merge_split_shfl<B>(x, j, keep_small);
-            } else {
-                merge_split_smem<B>(x, s_x, P, t, partner, true, keep_small);
-            }
-            bitonic_merge<B>(x);
-            if (stage_ctr && t == 0) atomicAdd(stage_ctr, 1ull);
-        }
-    }
-    store_block<B>(x, keys, vals, n, t, active);
+    net::btn_block<B>(keys, vals, n, p, s_x, stage_ctr);
 }
 
-// OET: p threads (any p); p rounds; round r pairs blocks (j, j+1) with
-// j = r mod 2, the lower block keeping the smaller half. Exchanges go through
-// shared memory.
+// OET: one CTA, p threads hold the blocks.
 template <int B>
-__global__ void k_oet(uint32_t* keys, uint32_t* vals, uint32_t n, int p, unsigned long long* stage_ctr) {
+__global__ void __launch_bounds__(B <= 16 ? 1024 : 512)
+    k_oet(uint32_t* keys, uint32_t* vals, uint32_t n, int p, unsigned long long* stage_ctr) {
     extern __shared__ __align__(16) uint64_t s_x[];
-    const int t = threadIdx.x;
-    const int P = blockDim.x;
-    const bool active = t < p;
-    uint64_t x[B];
-    load_block<B>(x, keys, n, t);
-    local_sort<B>(x);
-    for (int r = 0; r < p; ++r) {
-        const bool lower = ((t - r) & 1) == 0;  // t = j with j = r mod 2
-        const int partner = lower ? t + 1 : t - 1;
-        const bool exchange = active && partner >= 0 && partner < p;
-        merge_split_smem<B>(x, s_x, P, t, partner, exchange, lower);
-        if (exchange) bitonic_merge<B>(x);
-        if (stage_ctr && t == 0) atomicAdd(stage_ctr, 1ull);
-    }
-    store_block<B>(x, keys, vals, n, t, active);
+    net::oet_block<B>(keys, vals, n, p, s_x, stage_ctr);
 }
 
 int next_pow2(uint32_t v) {

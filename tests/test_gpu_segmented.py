@@ -1,0 +1,147 @@
+"""GPU parity of the batched segmented sort against the oracle (bit-exact):
+every routing class (OET, warp BTN, CTA BTN, clusters of 1/2/4/8 CTAs, and the
+long-segment path), empty and one-key segments, key ranges, payloads, graph
+reuse, error paths, and the full 200,000-length workload capped at 2^28 keys."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from gen import workloads
+from tests._util import to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+CLASS_EDGES = [0, 1, 2, 3, 31, 32, 33, 255, 256, 257, 4095, 4096, 4097, 8191, 8192, 8193, 16384, 16385,
+               32768, 32769, 65535, 65536]
+
+
+def make(lengths, seed, bits=32):
+    lengths = np.asarray(lengths, dtype=np.uint64)
+    off = np.zeros(lengths.size + 1, np.uint64)
+    off[1:] = np.cumsum(lengths)
+    n = int(off[-1])
+    keys = gen.uniform_u32(n, bits, seed, 0) if n else np.zeros(0, np.uint32)
+    vals = np.arange(n, dtype=np.uint32)
+    return keys, vals, off
+
+
+def run(isort, keys, vals, off, key_bits=32):
+    import torch
+
+    tk = to_dev(keys)
+    tv = None if vals is None else to_dev(vals)
+    to = to_dev(off)
+    isort.segmented(tk, tv, to, key_bits)
+    torch.cuda.synchronize()
+    return to_np(tk, np.uint32), (None if vals is None else to_np(tv, np.uint32))
+
+
+def check(isort, keys, vals, off, key_bits=32):
+    gk, gv = run(isort, keys, vals, off, key_bits)
+    rk, rv = oracle.segmented(keys, vals, off, key_bits, 8)
+    assert np.array_equal(gk, rk)
+    if vals is not None:
+        assert np.array_equal(gv, rv)
+
+
+def test_every_class_edge(cuda_lib):
+    lengths = CLASS_EDGES + CLASS_EDGES[::-1]
+    keys, vals, off = make(lengths, 5)
+    keys[::3] = keys[7]  # ties across and within segments
+    check(cuda_lib, keys, vals, off)
+    check(cuda_lib, keys, None, off)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_random_lengths(cuda_lib, seed):
+    r = np.random.default_rng(seed)
+    lengths = np.concatenate([r.integers(0, 40, 300), r.integers(30, 300, 100), r.integers(250, 5000, 40),
+                              r.integers(4000, 66000, 12)])
+    r.shuffle(lengths)
+    keys, vals, off = make(lengths, 10 + seed)
+    check(cuda_lib, keys, vals, off)
+
+
+@pytest.mark.parametrize("key_bits", [8, 16, 20, 31])
+def test_key_bits(cuda_lib, key_bits):
+    lengths = [17, 200, 3000, 9000, 20000, 40000, 70000]
+    keys, vals, off = make(lengths, 30 + key_bits, key_bits)
+    check(cuda_lib, keys, vals, off, key_bits)
+
+
+def test_skewed_keys(cuda_lib):
+    lengths = [31, 250, 4000, 8000, 30000, 60000]
+    keys, vals, off = make(lengths, 4)
+    keys[:] = gen.zipf_u32(keys.size, 1.1, 9, 10)
+    check(cuda_lib, keys, vals, off)
+
+
+def test_long_segments_host_path(cuda_lib):
+    lengths = [5, 70000, 3, 200001, 66000]
+    keys, vals, off = make(lengths, 41)
+    check(cuda_lib, keys, vals, off)
+
+
+def test_graph_reuse_different_buffers(cuda_lib):
+    for seed, lengths in ((51, [10, 300, 5000, 20000]), (52, [40000, 1, 33, 257]), (53, [10, 300, 5000, 20000])):
+        keys, vals, off = make(lengths, seed)
+        check(cuda_lib, keys, vals, off)
+
+
+def test_key_range_segment_left_unchanged(cuda_lib):
+    import torch
+
+    lengths = [20, 100, 1000, 10000, 50000]
+    keys, vals, off = make(lengths, 61, 16)
+    bad_seg = [1, 3]  # a warp-BTN segment and a cluster segment
+    for s in bad_seg:
+        keys[int(off[s]) + 5] = 1 << 16
+    tk, tv, to = to_dev(keys), to_dev(vals), to_dev(off)
+    with pytest.raises(cuda_lib.IsortError) as e:
+        cuda_lib.segmented(tk, tv, to, 16)
+    assert e.value.code == cuda_lib.KEY_RANGE
+    torch.cuda.synchronize()
+    gk, gv = to_np(tk, np.uint32), to_np(tv, np.uint32)
+    for s in range(len(lengths)):
+        a, b = int(off[s]), int(off[s + 1])
+        if s in bad_seg:
+            assert np.array_equal(gk[a:b], keys[a:b]) and np.array_equal(gv[a:b], vals[a:b])
+        else:
+            rk, rv = oracle.lsd(keys[a:b], vals[a:b], 16, 8)
+            assert np.array_equal(gk[a:b], rk) and np.array_equal(gv[a:b], rv)
+
+
+def test_decreasing_offsets_rejected(cuda_lib):
+    keys, vals, off = make([10, 10, 10], 71)
+    off[2] = 5
+    with pytest.raises(cuda_lib.IsortError) as e:
+        run(cuda_lib, keys, vals, off)
+    assert e.value.code == cuda_lib.INVALID_ARG
+
+
+def test_async_mode_long_segment_unsupported(cuda_lib):
+    import torch
+
+    keys, vals, off = make([100, 70000], 72)
+    tk, tv, to = to_dev(keys), to_dev(vals), to_dev(off)
+    cuda_lib.device_status(clear=True)
+    cuda_lib.set_sync(False)
+    try:
+        cuda_lib.segmented(tk, tv, to, 32)
+        assert cuda_lib.device_status(clear=True) == cuda_lib.UNSUPPORTED
+    finally:
+        cuda_lib.set_sync(True)
+    torch.cuda.synchronize()
+    gk = to_np(tk, np.uint32)
+    rk, _ = oracle.lsd(keys[:100], None, 32, 8)
+    assert np.array_equal(gk[:100], rk)  # the short segment is still sorted
+
+
+def test_full_segmented_workload(cuda_lib):
+    """200,000 log-uniform lengths on [2, 65,536] (seed 4) capped at 2^28 keys,
+    u32 keys + payload: bit-exact against the oracle."""
+    keys, vals, off = workloads.segmented()
+    gk, gv = run(cuda_lib, keys, vals, off)
+    rk, rv = oracle.segmented(keys, vals, off, 32, 8)
+    assert np.array_equal(gk, rk) and np.array_equal(gv, rv)

@@ -41,7 +41,7 @@ def test_first_1024_of_small_uniform(cuda_lib, fn):
 def test_btn_stage_count_and_result(cuda_lib, p):
     lg = int(math.log2(p))
     for n in sorted({1, 2, p, p + 1, 3 * p - 1, min(8 * p, 16384), min(32 * p, 16384)}):
-        if n > 32 * p:
+        if n > 32 * p or (p > 512 and n > 16 * p):
             continue
         keys = gen.uniform_u32(n, 6, n + p, 0)  # heavy ties: stability matters
         vals = np.arange(n, dtype=np.uint32)
