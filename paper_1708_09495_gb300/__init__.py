@@ -58,6 +58,7 @@ SIGNATURES = [
     ("isort_btn_p", _i32, [_vp, _vp, _sz, _i32, _vp, _vp]),
     ("isort_oet_p", _i32, [_vp, _vp, _sz, _i32, _vp, _vp]),
     ("isort_segmented", _i32, [_vp, _vp, _vp, _sz, _i32, _vp]),
+    ("isort_radix_noalloc", _i32, [_vp, _vp, _sz, _i32, _i32, _vp]),
     ("isort_set_sync", _i32, [_i32]),
     ("isort_device_status", _i32, [_i32, _vp]),
     ("isort_set_spin_limit", _i32, [_u64]),

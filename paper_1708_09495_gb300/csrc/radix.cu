@@ -862,6 +862,97 @@ isort_status radix_sort_u32_device(const uint32_t* kin, const uint32_t* vin, uin
     return radix_device<uint32_t>(kin, vin, kout, vout, n, key_bits, rb, s);
 }
 
+// Scratch an in-place sort of n u32 keys (+ payload) needs when the caller
+// provides it: the control block followed by the ping-pong buffers.
+size_t radix_u32_inplace_workspace_bytes(size_t n, int key_bits, int rb, bool vals) {
+    const int rounds = (key_bits + rb - 1) / rb;
+    const int bins = 1 << rb;
+    const int sh = bins <= 256 ? tune().shape_small : tune().shape_large;
+    const uint32_t tile = (uint32_t)shape_tile(sh);
+    const uint32_t num_tiles = (uint32_t)((n + tile - 1) / tile);
+    const int nbuf = (rounds % 2 == 0 || rounds == 1) ? 1 : 2;
+    const size_t buf_bytes = align_up(n * 4, 256) + (vals ? align_up(n * 4, 256) : 0);
+    return layout_ctl(nullptr, rounds, bins, num_tiles, true).bytes + (size_t)nbuf * buf_bytes;
+}
+
+// The in-place sort of isort_radix, with `ws` (ws_bytes, 256-byte aligned,
+// device memory) as its only scratch: no memory is allocated. The control
+// block at the head of ws is cleared here. *d_status points at the call's
+// device status word inside ws once the work is enqueued.
+isort_status radix_u32_inplace_in_workspace(uint32_t* keys, uint32_t* vals, size_t n, int key_bits, int rb,
+                                            unsigned char* ws, size_t ws_bytes, cudaStream_t s,
+                                            const uint32_t** d_status) {
+    const int rounds = (key_bits + rb - 1) / rb;
+    const int bins = 1 << rb;
+    const bool hv = vals != nullptr;
+    const int sh = bins <= 256 ? tune().shape_small : tune().shape_large;
+    const uint32_t tile = (uint32_t)shape_tile(sh);
+    const uint32_t num_tiles = (uint32_t)((n + tile - 1) / tile);
+    if (radix_u32_inplace_workspace_bytes(n, key_bits, rb, hv) > ws_bytes) return ISORT_ERR_UNSUPPORTED;
+    Ctl c = layout_ctl(ws, rounds, bins, num_tiles, true);
+    const size_t buf_bytes = align_up(n * 4, 256) + (hv ? align_up(n * 4, 256) : 0);
+    uint32_t* wk[2];
+    uint32_t* wv[2];
+    for (int i = 0; i < 2; ++i) {
+        unsigned char* p = ws + c.bytes + (size_t)i * buf_bytes;
+        wk[i] = reinterpret_cast<uint32_t*>(p);
+        wv[i] = hv ? reinterpret_cast<uint32_t*>(p + align_up(n * 4, 256)) : nullptr;
+    }
+    *d_status = c.status;
+    ISORT_TRY_CUDA(cudaMemsetAsync(ws, 0, c.zero_bytes, s));
+    isort_status st = launch_hist<uint32_t>(keys, n, 0, rb, key_bits, rounds, c.hist, c.key_or, c.status, s);
+    if (st != ISORT_OK) return st;
+    st = launch_scan(c.hist, c.offs, rounds, bins, c.key_or, key_bits, 32, c.status, s);
+    if (st != ISORT_OK) return st;
+    const uint32_t* src_k = keys;
+    const uint32_t* src_v = vals;
+    for (int d = 0; d < rounds; ++d) {
+        uint32_t* dk;
+        uint32_t* dv;
+        if (rounds == 1) {
+            dk = wk[0];
+            dv = wv[0];
+        } else if (rounds % 2 == 0) {
+            dk = (d % 2) == 1 ? keys : wk[0];
+            dv = (d % 2) == 1 ? vals : wv[0];
+        } else if (d == rounds - 1) {
+            dk = keys;
+            dv = vals;
+        } else {
+            dk = wk[d % 2];
+            dv = wv[d % 2];
+        }
+        const int shift = d * rb;
+        const int width = std::min(rb, key_bits - shift);
+        PassArgs a;
+        a.keys_in = src_k;
+        a.vals_in = src_v;
+        a.keys_out = dk;
+        a.vals_out = dv;
+        a.n = (uint32_t)n;
+        a.shift = shift;
+        a.width = width;
+        a.bins = 1 << width;
+        a.bin_off = c.offs + (size_t)d * bins;
+        a.lookback = c.lookback + (size_t)d * num_tiles * bins;
+        a.tile_counter = c.tile_ctr + d;
+        a.status = c.status;
+        a.num_tiles = num_tiles;
+        a.limit_ns = spin_limit_ns();
+        a.stall_tile = -1;
+        a.use_bulk = (((uintptr_t)src_k % 16) == 0) && (!hv || ((uintptr_t)src_v % 16) == 0);
+        st = launch_round_dispatch<uint32_t>(sh, hv, a, s);
+        if (st != ISORT_OK) return st;
+        src_k = dk;
+        src_v = dv;
+    }
+    if (rounds == 1) {
+        ISORT_TRY_CUDA(cudaMemcpyAsync(keys, wk[0], n * 4, cudaMemcpyDeviceToDevice, s));
+        if (hv) ISORT_TRY_CUDA(cudaMemcpyAsync(vals, wv[0], n * 4, cudaMemcpyDeviceToDevice, s));
+    }
+    return ISORT_OK;
+}
+
 template <typename K>
 isort_status count_round_entry(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n, int shift,
                                       int width, void* stream) {
