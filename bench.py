@@ -232,17 +232,22 @@ def run_ours(args):
     ms_max = float(ms_t.item())
     value = world * args.steps * N / (ms_max * 1e-3) / 1e9
 
-    # dominant kernel: the rank-and-scatter round
+    # dominant kernel: the rank-and-scatter launch of a round (chunked rounds:
+    # "downsweep"; single-pass rounds: "onesweep"). Algorithmic bytes per
+    # launch: one read and one write of n keys and payloads.
     peak, peak_kind = peaks()
-    rl, rms = prof.get("onesweep", (0, 0.0))
+    round_kernel = "downsweep" if "downsweep" in prof else "onesweep"
+    rl, rms = prof.get(round_kernel, (0, 0.0))
     avg_round_ms = rms / max(rl, 1)
     achieved = N * ROUND_BYTES_PER_KEY / (avg_round_ms * 1e-3) / 1e9 if rl else None
     traffic = None
-    tpath = os.path.join(ROOT, "profiles", "onesweep_traffic.json")
+    tpath = os.path.join(ROOT, "profiles", f"{round_kernel}_traffic.json")
     if os.path.exists(tpath):
         try:
             with open(tpath) as f:
-                traffic = json.load(f).get("bytes_per_launch")
+                t = json.load(f)
+            if t.get("log2n") == int(round(np.log2(N))) and t.get("radix_bits") == RADIX_BITS:
+                traffic = t.get("bytes_per_launch")
         except Exception:
             traffic = None
     kernels = {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in prof.items()}
@@ -286,7 +291,8 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                         "kernel": "onesweep (one count-sort round)", "peak_kind": peak_kind,
+                         "kernel": f"{round_kernel} (rank and scatter of one count-sort round)",
+                         "peak_kind": peak_kind,
                          "whole_sort_frac": N * BYTES_PER_KEY / (ms_max / args.steps * 1e-3) / 1e9 / peak},
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -193,22 +193,27 @@ ISORT_API isort_status isort_device_status(int clear, void* stream);
 ISORT_API isort_status isort_set_spin_limit(uint64_t microseconds);
 
 /* ---------------------------------------------------------------------------
- * Fault injection for tests: isort_debug_stall_tile(t) makes look-back tile t of
- * the next radix round never publish its counts, so that its successors' waits
- * run out (t < 0 disables). It only ever causes bounded waits.
+ * Fault injection for tests: isort_debug_stall_tile(t) makes the next radix
+ * sort run its rounds in the single-pass form (tiles resolve their offsets by
+ * looking back at earlier tiles' published counts) with tile t of the first
+ * round never publishing, so that its successors' waits run out (t < 0
+ * disables). It only ever causes bounded waits.
  * ------------------------------------------------------------------------- */
 ISORT_API isort_status isort_debug_stall_tile(int64_t tile);
 
 /* ---------------------------------------------------------------------------
  * Introspection.
  * isort_launch_count: number of kernels this library has launched so far in
- *   this process.
+ *   this process. isort_last_error_string: see its declaration.
  * isort_profile_enable(1): record CUDA events around every kernel launch.
  * isort_profile_read: waits for the recorded events, writes up to max entries
  *   (one per kernel name: launches and total milliseconds) and clears the
  *   record; returns the number of entries written.
  * ------------------------------------------------------------------------- */
 ISORT_API uint64_t isort_launch_count(void);
+/* Text of the last CUDA error or device-side status this thread's calls met
+ * ("" if none); valid until the thread's next call. */
+ISORT_API const char* isort_last_error_string(void);
 typedef struct {
     char name[48];
     uint64_t launches;

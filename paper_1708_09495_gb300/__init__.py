@@ -64,6 +64,7 @@ SIGNATURES = [
     ("isort_set_spin_limit", _i32, [_u64]),
     ("isort_debug_stall_tile", _i32, [_i64]),
     ("isort_launch_count", _u64, []),
+    ("isort_last_error_string", ctypes.c_char_p, []),
     ("isort_profile_enable", _i32, [_i32]),
     ("isort_profile_read", _i32, [ctypes.POINTER(KernelTime), _i32]),
 ]
@@ -75,7 +76,14 @@ _lib = None
 class IsortError(RuntimeError):
     def __init__(self, code: int, where: str = ""):
         self.code = code
-        super().__init__(f"{where}: {STATUS.get(code, code)}" if where else STATUS.get(code, str(code)))
+        detail = ""
+        try:
+            if _lib is not None:
+                detail = (_lib.isort_last_error_string() or b"").decode()
+        except Exception:
+            detail = ""
+        msg = f"{where}: {STATUS.get(code, code)}" if where else STATUS.get(code, str(code))
+        super().__init__(f"{msg} ({detail})" if detail else msg)
 
 
 def load(path: str | None = None):

@@ -35,6 +35,9 @@ struct Tune {
     int rank_mode = 1;    // 0: match-any ranking, 1: per-bit ballot ranking
     int shape_small = 4;  // launch shape for digits of <= 8 bits
     int shape_large = 1;  // launch shape for wider digits
+    int algo = 1;         // 0: single-pass rounds with look-back, 1: chunked reduce-then-scan rounds
+    int sweep_small = 3;  // chunked-round launch shape, digits of <= 8 bits
+    int sweep_large = 2;  // chunked-round launch shape, wider digits
 };
 
 static Tune load_tune() {
@@ -51,11 +54,16 @@ static Tune load_tune() {
         else if (!strcmp(key, "rank")) t.rank_mode = val;
         else if (!strcmp(key, "shape8")) t.shape_small = val;
         else if (!strcmp(key, "shape11")) t.shape_large = val;
+        else if (!strcmp(key, "algo")) t.algo = val;
+        else if (!strcmp(key, "sweep8")) t.sweep_small = val;
+        else if (!strcmp(key, "sweep11")) t.sweep_large = val;
         p += used;
         if (*p == ',') ++p;
     }
-    if (t.shape_small < 0 || t.shape_small >= 6) t.shape_small = 4;
-    if (t.shape_large < 0 || t.shape_large >= 6) t.shape_large = 1;
+    if (t.sweep_small < 0 || t.sweep_small >= 4) t.sweep_small = 3;
+    if (t.sweep_large < 0 || t.sweep_large >= 4) t.sweep_large = 2;
+    if (t.shape_small < 0 || t.shape_small >= 13) t.shape_small = 4;
+    if (t.shape_large < 0 || t.shape_large >= 13) t.shape_large = 1;
     return t;
 }
 
@@ -110,7 +118,21 @@ __device__ __forceinline__ void hist_count_key_warp(K k, uint32_t* s_hist, int s
     }
 }
 
-template <typename K, bool AGG>
+// Compile-time form for the common (radix bits, key bits) pairs: the digit
+// shifts and masks fold into constants.
+template <typename K, int RB, int KB>
+__device__ __forceinline__ void hist_count_key_c(K k, uint32_t* s_hist) {
+    constexpr int R = (KB + RB - 1) / RB;
+#pragma unroll
+    for (int d = 0; d < R; ++d) {
+        const int w = (KB - d * RB) < RB ? (KB - d * RB) : RB;
+        const uint32_t dig = (uint32_t)(k >> (d * RB)) & ((1u << w) - 1u);
+        atomicAdd(&s_hist[d * (1 << RB) + dig], 1u);
+    }
+}
+
+// RB, KB > 0: compile-time digit layout (shift0 must be 0); 0: runtime.
+template <typename K, bool AGG, int RB = 0, int KB = 0>
 __global__ void __launch_bounds__(kHistThreads) k_digit_hist(HistArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int bins = 1 << a.radix_bits;
@@ -119,6 +141,10 @@ __global__ void __launch_bounds__(kHistThreads) k_digit_hist(HistArgs a) {
     uint64_t* bars = reinterpret_cast<uint64_t*>(s_hist + align_up_dev(nh, 2));
     const K* keys = static_cast<const K*>(a.keys);
     const int tid = threadIdx.x;
+    if ((size_t)(reinterpret_cast<unsigned char*>(bars + kHistStages) - smem) > dynamic_smem_size()) {
+        if (tid == 0) set_status(a.status, kStatBounds);
+        return;
+    }
 
     for (int i = tid; i < nh; i += kHistThreads) s_hist[i] = 0;
     if (tid == 0) {
@@ -168,7 +194,9 @@ __global__ void __launch_bounds__(kHistThreads) k_digit_hist(HistArgs a) {
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     acc |= (K)w[e];
-                    if constexpr (AGG)
+                    if constexpr (RB > 0)
+                        hist_count_key_c<K, RB, KB>((K)w[e], s_hist);
+                    else if constexpr (AGG)
                         hist_count_key_warp<K>((K)w[e], s_hist, a.shift0, a.rounds, a.radix_bits, a.key_bits, bins);
                     else
                         hist_count_key<K>((K)w[e], s_hist, a.shift0, a.rounds, a.radix_bits, a.key_bits, bins);
@@ -178,7 +206,9 @@ __global__ void __launch_bounds__(kHistThreads) k_digit_hist(HistArgs a) {
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
                     acc |= w[e];
-                    if constexpr (AGG)
+                    if constexpr (RB > 0)
+                        hist_count_key_c<K, RB, KB>(w[e], s_hist);
+                    else if constexpr (AGG)
                         hist_count_key_warp<K>(w[e], s_hist, a.shift0, a.rounds, a.radix_bits, a.key_bits, bins);
                     else
                         hist_count_key<K>(w[e], s_hist, a.shift0, a.rounds, a.radix_bits, a.key_bits, bins);
@@ -378,6 +408,10 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
     uint64_t* bars = reinterpret_cast<uint64_t*>(s_delta + bins);
     uint32_t* s_warp_scan = reinterpret_cast<uint32_t*>(bars + 2);
     volatile uint32_t& s_next_tile = s_warp_scan[WARPS];
+    if ((size_t)(reinterpret_cast<unsigned char*>(s_warp_scan + WARPS + 1) - smem) > dynamic_smem_size()) {
+        if (threadIdx.x == 0) set_status(a.status, kStatBounds);
+        return;
+    }
 
     // An earlier step (the key-range check) failed: do nothing, uniformly.
     if (*(volatile uint32_t*)a.status != 0) return;
@@ -574,13 +608,568 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
 }
 
 // ----------------------------------------------------------------------------
+// One count-sort round, second form: one CTA per tile (tiles taken in order
+// from an atomic counter), keys and payloads loaded straight into registers,
+// several CTAs per SM so that one CTA's look-back wait overlaps another's
+// ranking. The tile's digit counts are taken first with shared atomics
+// ("early counts") and published before the ranking, so later tiles rarely
+// wait on this one.
+// ----------------------------------------------------------------------------
+template <typename K, bool VALS, int THREADS, int ITEMS>
+struct DirectCfg {
+    static constexpr int kWarps = THREADS / 32;
+    static constexpr int kTile = THREADS * ITEMS;
+    static size_t smem_bytes(int bins) {
+        size_t b = (size_t)kTile * sizeof(K) + (VALS ? (size_t)kTile * 4 : 0);  // staging
+        b += (size_t)kWarps * bins * 4;                                          // per-warp counts -> offsets
+        b += align_up((size_t)kWarps * bins * 2, 16);                            // per-warp running ranks
+        b += (size_t)bins * 4 * 2;                                               // digit starts, deltas
+        b += (size_t)kWarps * 4 + 16;
+        return align_up(b, 128);
+    }
+};
+
+template <typename K, bool VALS, int THREADS, int ITEMS, int RANK>
+__global__ void __launch_bounds__(THREADS, ((ITEMS >= 24 ? 512 : 1024) / THREADS) > 0
+                                                ? ((ITEMS >= 24 ? 512 : 1024) / THREADS)
+                                                : 1) k_onesweep_direct(PassArgs a) {
+    using Cfg = DirectCfg<K, VALS, THREADS, ITEMS>;
+    constexpr int WARPS = Cfg::kWarps;
+    constexpr int TILE = Cfg::kTile;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int bins = a.bins;
+    const uint32_t dmask = (uint32_t)bins - 1u;
+    K* s_keys = reinterpret_cast<K*>(smem);
+    uint32_t* s_vals = reinterpret_cast<uint32_t*>(smem + (size_t)TILE * sizeof(K));
+    uint32_t* s_whist = reinterpret_cast<uint32_t*>(smem + (size_t)TILE * sizeof(K) + (VALS ? (size_t)TILE * 4 : 0));
+    uint16_t* s_cnt = reinterpret_cast<uint16_t*>(s_whist + (size_t)WARPS * bins);
+    uint32_t* s_bin_start = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(s_cnt) +
+                                                        align_up_dev((size_t)WARPS * bins * 2, 16));
+    uint32_t* s_delta = s_bin_start + bins;
+    uint32_t* s_warp_scan = s_delta + bins;
+    volatile uint32_t& s_tile = s_warp_scan[WARPS];
+    if ((size_t)(reinterpret_cast<unsigned char*>(s_warp_scan + WARPS + 1) - smem) > dynamic_smem_size()) {
+        if (threadIdx.x == 0) set_status(a.status, kStatBounds);
+        return;
+    }
+
+    if (*(volatile uint32_t*)a.status != 0) return;  // an earlier step failed
+    if (tid == 0) s_tile = atomicAdd(a.tile_counter, 1u);
+    for (int i = tid; i < WARPS * bins; i += THREADS) {
+        s_whist[i] = 0;
+        s_cnt[i] = 0;
+    }
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= a.num_tiles) return;
+    const uint32_t tile_base = tile * (uint32_t)TILE;
+    const uint32_t tile_n = min((uint32_t)TILE, a.n - tile_base);
+    const K* keys_in = static_cast<const K*>(a.keys_in) + tile_base;
+    const uint32_t* vals_in = VALS ? a.vals_in + tile_base : nullptr;
+    K* keys_out = static_cast<K*>(a.keys_out);
+
+    K kreg[ITEMS];
+    uint32_t vreg[ITEMS];
+    uint32_t rank[ITEMS];
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t j = (uint32_t)(warp * ITEMS * 32 + i * 32 + lane);
+        kreg[i] = j < tile_n ? keys_in[j] : (K)0;
+        if constexpr (VALS) vreg[i] = j < tile_n ? vals_in[j] : 0u;
+    }
+    const bool stalled = (long long)tile == a.stall_tile;  // fault injection: never publish
+    // early counts
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t j = (uint32_t)(warp * ITEMS * 32 + i * 32 + lane);
+        if (j < tile_n) atomicAdd(&s_whist[warp * bins + ((uint32_t)(kreg[i] >> a.shift) & dmask)], 1u);
+    }
+    __syncthreads();
+    uint32_t* lb_tile = a.lookback + (size_t)tile * bins;
+    for (int d = tid; d < bins; d += THREADS) {
+        uint32_t sum = 0;
+#pragma unroll 4
+        for (int w = 0; w < WARPS; ++w) {
+            const uint32_t c = s_whist[w * bins + d];
+            s_whist[w * bins + d] = sum;
+            sum += c;
+        }
+        s_bin_start[d] = sum;
+        s_delta[d] = sum;
+        if (!stalled) st_relaxed(&lb_tile[d], (tile == 0 ? kFlagInc : kFlagAgg) | sum);
+    }
+    if (stalled) {
+        __syncthreads();
+        block_exclusive_scan<THREADS>(s_bin_start, bins, s_warp_scan);
+        return;
+    }
+    // decoupled look-back (windowed, bounded), right after publishing, so that
+    // this tile's inclusive counts appear as early as possible; the warps
+    // without look-back work go on to rank their keys meanwhile
+    constexpr int kWin = 8;
+    int lfail = 0;
+    for (int d = tid; d < bins; d += THREADS) {
+        const uint32_t total = s_delta[d];
+        uint32_t excl = 0;
+        if (tile > 0) {
+            long long t = (long long)tile - 1;
+            uint64_t t0 = 0;
+            uint32_t spins = 0;
+            bool done = false;
+            while (!done && t >= 0) {
+                uint32_t w[kWin];
+#pragma unroll
+                for (int q = 0; q < kWin; ++q)
+                    w[q] = t - q >= 0 ? ld_relaxed(&a.lookback[(size_t)(t - q) * bins + d]) : kFlagInc;
+                int used = 0;
+                bool stall = false;
+#pragma unroll
+                for (int q = 0; q < kWin; ++q) {
+                    if (done || stall) continue;
+                    const uint32_t flag = w[q] & ~kCountMask;
+                    if (flag == 0) { stall = true; continue; }
+                    excl += w[q] & kCountMask;
+                    ++used;
+                    if (flag == kFlagInc) done = true;
+                }
+                t -= used;
+                if (stall && !done) {
+                    if (t0 == 0) t0 = global_timer_ns();
+                    else if (global_timer_ns() - t0 > a.limit_ns) { lfail = 1; break; }
+                    if ((++spins & 31u) == 0 && ld_relaxed(a.status) != 0) { lfail = 1; break; }
+                    __nanosleep(64);
+                }
+            }
+            if (lfail) set_status(a.status, kStatTimeout);
+            __threadfence();
+            st_relaxed(&lb_tile[d], kFlagInc | ((excl + total) & kCountMask));
+        }
+        s_delta[d] = a.bin_off[d] + excl;  // the tile's digit start is subtracted after the scan
+    }
+    // rank each key among equal digits of its warp, in input order
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t j = (uint32_t)(warp * ITEMS * 32 + i * 32 + lane);
+        const bool valid = j < tile_n;
+        const uint32_t d = (uint32_t)(kreg[i] >> a.shift) & dmask;
+        const uint32_t peers = warp_peers<RANK>(d, valid, a.width);
+        const uint32_t below = (uint32_t)__popc(peers & lanemask_lt());
+        const uint32_t c = valid ? (uint32_t)s_cnt[warp * bins + d] : 0u;
+        rank[i] = c + below;
+        __syncwarp();
+        if (valid && below + 1 == (uint32_t)__popc(peers)) s_cnt[warp * bins + d] = (uint16_t)(c + below + 1);
+        __syncwarp();
+    }
+    __syncthreads();
+    block_exclusive_scan<THREADS>(s_bin_start, bins, s_warp_scan);
+    for (int d = tid; d < bins; d += THREADS) s_delta[d] -= s_bin_start[d];
+    if (tid == 0 && ld_relaxed(a.status) != 0) lfail = 1;
+    if (__syncthreads_or(lfail)) return;
+    // stage by digit
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t j = (uint32_t)(warp * ITEMS * 32 + i * 32 + lane);
+        if (j < tile_n) {
+            const uint32_t d = (uint32_t)(kreg[i] >> a.shift) & dmask;
+            const uint32_t pos = s_bin_start[d] + s_whist[warp * bins + d] + rank[i];
+            if (pos < (uint32_t)TILE) {
+                s_keys[pos] = kreg[i];
+                if constexpr (VALS) s_vals[pos] = vreg[i];
+            }
+        }
+    }
+    __syncthreads();
+    for (uint32_t j = tid; j < tile_n; j += THREADS) {
+        const K k = s_keys[j];
+        const uint32_t d = (uint32_t)(k >> a.shift) & dmask;
+        const uint32_t dst = s_delta[d] + j;
+        if (dst < a.n) {
+            keys_out[dst] = k;
+            if constexpr (VALS) a.vals_out[dst] = s_vals[j];
+        } else {
+            set_status(a.status, kStatBounds);
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Count-sort rounds by chunked reduce-then-scan.
+//
+// The round's input is cut into C contiguous chunks of whole tiles, one per
+// persistent CTA. k_chunk_hist counts each chunk's digits (one read of the
+// keys); k_chunk_scan turns the C x 2^rb counts into the first output position
+// of every digit for every chunk (digit-major prefix, then chunk order);
+// k_downsweep then streams its chunk tile by tile -- the next tile's keys and
+// payloads copied into shared memory by the bulk-copy engine while the current
+// tile is ranked -- and keeps one running output position per digit in shared
+// memory. Chunks never wait for one another, so the round runs at the rate of
+// the memory system; the price is the extra read of the keys per round.
+// ----------------------------------------------------------------------------
+constexpr int kChunkHistThreads = 512;
+
+template <typename K>
+__global__ void __launch_bounds__(kChunkHistThreads) k_chunk_hist(const K* __restrict__ keys, uint32_t n, int shift,
+                                                                  int width, uint32_t chunk_keys, int nsub,
+                                                                  uint32_t* __restrict__ hist,
+                                                                  unsigned long long* key_or) {
+    extern __shared__ __align__(16) uint32_t s_h[];  // [nsub][bins]
+    const int bins = 1 << width;
+    const uint32_t mask = (uint32_t)bins - 1u;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < nsub * bins; i += kChunkHistThreads) s_h[i] = 0;
+    __syncthreads();
+    uint32_t* my = s_h + (size_t)((tid >> 5) % nsub) * bins;
+    const uint32_t lo = blockIdx.x * chunk_keys;
+    const uint32_t hi = min(n, lo + chunk_keys);
+    K acc = 0;
+    if (lo < hi) {
+        const K* base = keys + lo;
+        const uint32_t cnt = hi - lo;
+        constexpr int per_vec = 16 / sizeof(K);
+        const bool vec = ((uintptr_t)base % 16) == 0;
+        const uint32_t nvec = vec ? cnt / per_vec : 0;
+        const uint4* v4 = reinterpret_cast<const uint4*>(base);
+#pragma unroll 4
+        for (uint32_t i = tid; i < nvec; i += kChunkHistThreads) {
+            const uint4 v = __ldg(&v4[i]);
+            if constexpr (sizeof(K) == 4) {
+                const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    acc |= (K)w[e];
+                    atomicAdd(&my[(w[e] >> shift) & mask], 1u);
+                }
+            } else {
+                const K w[2] = {((K)v.y << 32) | v.x, ((K)v.w << 32) | v.z};
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    acc |= w[e];
+                    atomicAdd(&my[(uint32_t)(w[e] >> shift) & mask], 1u);
+                }
+            }
+        }
+        for (uint32_t i = nvec * per_vec + tid; i < cnt; i += kChunkHistThreads) {
+            const K k = base[i];
+            acc |= k;
+            atomicAdd(&my[(uint32_t)(k >> shift) & mask], 1u);
+        }
+    }
+    __syncthreads();
+    uint32_t* out = hist + (size_t)blockIdx.x * bins;
+    for (int d = tid; d < bins; d += kChunkHistThreads) {
+        uint32_t sum = 0;
+        for (int q = 0; q < nsub; ++q) sum += s_h[q * bins + d];
+        out[d] = sum;
+    }
+    if (key_or) {
+        const unsigned long long o = (unsigned long long)acc;
+        const uint32_t l = __reduce_or_sync(kFullMask, (uint32_t)o);
+        const uint32_t h = __reduce_or_sync(kFullMask, (uint32_t)(o >> 32));
+        if ((tid & 31) == 0 && (l | h)) atomicOr(key_or, ((unsigned long long)h << 32) | l);
+    }
+}
+
+// chunk_off[c][d] = (keys with a smaller digit) + (keys with digit d in chunks < c).
+// The 1024 threads form G = max(1, 1024 / bins) groups; group g owns a
+// contiguous run of chunks, so each thread sums (and later prefixes) only
+// C / G counts, with independent loads.
+constexpr int kChunkScanThreads = 1024;
+
+__global__ void __launch_bounds__(kChunkScanThreads) k_chunk_scan(const uint32_t* __restrict__ hist, int chunks,
+                                                                  int bins, uint32_t* __restrict__ chunk_off,
+                                                                  const unsigned long long* key_or, int key_bits,
+                                                                  int key_width, uint32_t* status) {
+    extern __shared__ __align__(16) uint32_t s_dyn[];  // [G][bins] group sums, then [bins] digit totals
+    __shared__ uint32_t s_warp[kChunkScanThreads / 32];
+    const int tid = threadIdx.x;
+    const int G = bins >= kChunkScanThreads ? 1 : kChunkScanThreads / bins;
+    const int per = (chunks + G - 1) / G;
+    uint32_t* s_part = s_dyn;
+    uint32_t* s_tot = s_dyn + (size_t)G * bins;
+    for (int x = tid; x < G * bins; x += kChunkScanThreads) {
+        const int g = x / bins, d = x % bins;
+        const int c0 = g * per, c1 = min(chunks, c0 + per);
+        uint32_t t = 0;
+#pragma unroll 8
+        for (int c = c0; c < c1; ++c) t += hist[(size_t)c * bins + d];
+        s_part[x] = t;
+    }
+    __syncthreads();
+    for (int d = tid; d < bins; d += kChunkScanThreads) {
+        uint32_t t = 0;
+        for (int g = 0; g < G; ++g) t += s_part[g * bins + d];
+        s_tot[d] = t;
+    }
+    __syncthreads();
+    block_exclusive_scan<kChunkScanThreads>(s_tot, bins, s_warp);
+    for (int x = tid; x < G * bins; x += kChunkScanThreads) {
+        const int g = x / bins, d = x % bins;
+        uint32_t run = s_tot[d];
+        for (int q = 0; q < g; ++q) run += s_part[q * bins + d];
+        const int c0 = g * per, c1 = min(chunks, c0 + per);
+#pragma unroll 8
+        for (int c = c0; c < c1; ++c) {
+            const uint32_t h = hist[(size_t)c * bins + d];
+            chunk_off[(size_t)c * bins + d] = run;
+            run += h;
+        }
+    }
+    if (key_or && tid == 0 && key_bits < key_width && ((*key_or) >> key_bits)) set_status(status, kStatKeyRange);
+}
+
+struct SweepArgs {
+    const void* keys_in;
+    const uint32_t* vals_in;
+    void* keys_out;
+    uint32_t* vals_out;
+    uint32_t n;
+    int shift;
+    int width;
+    int bins;
+    const uint32_t* chunk_off;  // [chunks][bins]
+    uint32_t chunk_tiles;
+    uint32_t num_tiles;
+    uint32_t* status;
+    uint64_t limit_ns;
+    int use_bulk;
+};
+
+template <typename K, bool VALS, int THREADS, int ITEMS>
+struct SweepCfg {
+    static constexpr int kWarps = THREADS / 32;
+    static constexpr int kTile = THREADS * ITEMS;
+    static constexpr size_t kBufBytes = (size_t)kTile * sizeof(K) + (VALS ? (size_t)kTile * 4 : 0);
+    static size_t smem_bytes(int bins) {
+        size_t b = 2 * kBufBytes;
+        b += align_up((size_t)kWarps * bins * 2, 16);  // per-warp digit counts (u16)
+        b += (size_t)kWarps * bins * 4;                // per-warp peer masks
+        b += (size_t)bins * 4 * 4;                     // tile digit starts, totals, running positions, deltas
+        b += 2 * 8 + (size_t)kWarps * 4 + 16;          // mbarriers, warp sums
+        return align_up(b, 128);
+    }
+};
+
+// Peers of this lane for a WIDTH-bit digit: the valid lanes whose digit
+// agrees with this lane's on every bit (one ballot per bit; m is all ones when
+// this lane's bit is set, so ~(bal ^ m) keeps the lanes that agree).
+template <int WIDTH>
+__device__ __forceinline__ uint32_t peers_of(uint32_t d, uint32_t valid_mask, int width) {
+    uint32_t peers = valid_mask;
+    if constexpr (WIDTH > 0) {
+#pragma unroll
+        for (int b = 0; b < WIDTH; ++b) {
+            const uint32_t bal = __ballot_sync(kFullMask, (d >> b) & 1u);
+            const uint32_t m = (uint32_t)((int32_t)(d << (31 - b)) >> 31);
+            peers &= ~(bal ^ m);
+        }
+    } else {
+        for (int b = 0; b < width; ++b) {
+            const uint32_t bal = __ballot_sync(kFullMask, (d >> b) & 1u);
+            const uint32_t m = (uint32_t)((int32_t)(d << (31 - b)) >> 31);
+            peers &= ~(bal ^ m);
+        }
+    }
+    return peers;
+}
+
+// One tile of a chunked round: rank, stage by digit, write out, advance the
+// chunk's running positions. FULL: the tile holds TILE keys (no bounds tests
+// on the tile's own indices). WIDTH > 0: the digit width at compile time.
+//
+// Ranking: peers (the lanes of a warp holding the same digit) come from a
+// per-warp mask word per digit: every lane ORs its lane bit into its digit's
+// word and, after a warp barrier, reads the word back. The result does not
+// depend on the order in which the atomics land. A per-warp 16-bit count per
+// digit carries the rank across the warp's items (input order: stable).
+template <typename K, bool VALS, int THREADS, int ITEMS, int WIDTH, bool FULL>
+__device__ __forceinline__ void sweep_tile(const SweepArgs& a, K* s_keys, uint32_t* s_vals, uint16_t* s_cnt,
+                                           uint32_t* s_match, uint32_t* s_start, uint32_t* s_tot, uint32_t* s_run,
+                                           uint32_t* s_delta, uint32_t* s_warp_scan, uint32_t tile_n) {
+    constexpr int WARPS = THREADS / 32;
+    constexpr int TILE = THREADS * ITEMS;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int bins = WIDTH > 0 ? (1 << WIDTH) : a.bins;
+    const uint32_t dmask = (uint32_t)bins - 1u;
+    const int shift = a.shift;
+    uint16_t* my_cnt = s_cnt + warp * bins;
+    uint32_t* my_match = s_match + warp * bins;
+    const uint32_t lt = lanemask_lt();
+    K kreg[ITEMS];
+    uint32_t vreg[ITEMS];
+    uint32_t rank[ITEMS];
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t j = (uint32_t)(warp * ITEMS * 32 + i * 32 + lane);
+        const bool valid = FULL || j < tile_n;
+        const K k = valid ? s_keys[j] : (K)0;
+        kreg[i] = k;
+        if constexpr (VALS) vreg[i] = valid ? s_vals[j] : 0u;
+        const uint32_t d = (uint32_t)(k >> shift) & dmask;
+        if (valid) atomicOr(&my_match[d], 1u << lane);
+        __syncwarp();
+        const uint32_t peers = valid ? my_match[d] : 0u;
+        const uint32_t c = valid ? (uint32_t)my_cnt[d] : 0u;
+        __syncwarp();
+        rank[i] = c + (uint32_t)__popc(peers & lt);
+        if (valid && (peers >> lane) == 1u) {  // the group's highest lane
+            my_cnt[d] = (uint16_t)(c + (uint32_t)__popc(peers));
+            my_match[d] = 0u;
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int d = tid; d < bins; d += THREADS) {
+        uint32_t sum = 0;
+#pragma unroll 4
+        for (int w = 0; w < WARPS; ++w) {
+            const uint32_t c = s_cnt[w * bins + d];
+            s_cnt[w * bins + d] = (uint16_t)sum;
+            sum += c;
+        }
+        s_start[d] = sum;
+        s_tot[d] = sum;
+    }
+    __syncthreads();
+    block_exclusive_scan<THREADS>(s_start, bins, s_warp_scan);
+    for (int d = tid; d < bins; d += THREADS) s_delta[d] = s_run[d] - s_start[d];
+    // stage keys by digit (over the tile's own buffer: its keys are in registers)
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t j = (uint32_t)(warp * ITEMS * 32 + i * 32 + lane);
+        if (FULL || j < tile_n) {
+            const uint32_t d = (uint32_t)(kreg[i] >> shift) & dmask;
+            const uint32_t pos = s_start[d] + my_cnt[d] + rank[i];
+            if (pos < (uint32_t)TILE) {
+                s_keys[pos] = kreg[i];
+                if constexpr (VALS) s_vals[pos] = vreg[i];
+            }
+        }
+    }
+    __syncthreads();
+    K* keys_out = static_cast<K*>(a.keys_out);
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t j = (uint32_t)(tid + i * THREADS);
+        if (FULL || j < tile_n) {
+            const K k = s_keys[j];
+            const uint32_t d = (uint32_t)(k >> shift) & dmask;
+            const uint32_t dst = s_delta[d] + j;
+            if (dst < a.n) {
+                keys_out[dst] = k;
+                if constexpr (VALS) a.vals_out[dst] = s_vals[j];
+            } else {
+                set_status(a.status, kStatBounds);
+            }
+        }
+    }
+    __syncthreads();
+    for (int d = tid; d < bins; d += THREADS) s_run[d] += s_tot[d];
+    for (int i = tid; i < WARPS * bins; i += THREADS) s_cnt[i] = 0;
+    __syncthreads();
+}
+
+template <typename K, bool VALS, int THREADS, int ITEMS, int WIDTH>
+__global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREADS) : 1) k_downsweep(SweepArgs a) {
+    using Cfg = SweepCfg<K, VALS, THREADS, ITEMS>;
+    constexpr int WARPS = Cfg::kWarps;
+    constexpr int TILE = Cfg::kTile;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int bins = a.bins;
+    const uint32_t dmask = (uint32_t)bins - 1u;
+    unsigned char* buf0 = smem;
+    uint16_t* s_cnt = reinterpret_cast<uint16_t*>(smem + 2 * Cfg::kBufBytes);
+    uint32_t* s_match = reinterpret_cast<uint32_t*>(smem + 2 * Cfg::kBufBytes +
+                                                    align_up_dev((size_t)WARPS * bins * 2, 16));
+    uint32_t* s_start = s_match + (size_t)WARPS * bins;
+    uint32_t* s_tot = s_start + bins;
+    uint32_t* s_run = s_tot + bins;
+    uint32_t* s_delta = s_run + bins;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(s_delta + bins);
+    uint32_t* s_warp_scan = reinterpret_cast<uint32_t*>(bars + 2);
+    // the layout must fit the launch's shared memory (uniform check)
+    if ((size_t)(reinterpret_cast<unsigned char*>(s_warp_scan + WARPS + 4) - smem) > dynamic_smem_size()) {
+        if (threadIdx.x == 0) set_status(a.status, kStatBounds);
+        return;
+    }
+
+    if (*(volatile uint32_t*)a.status != 0) return;  // an earlier step failed
+    const uint32_t t_begin = blockIdx.x * a.chunk_tiles;
+    const uint32_t t_end = min(a.num_tiles, t_begin + a.chunk_tiles);
+    if (t_begin >= t_end) return;
+    const K* keys_in = static_cast<const K*>(a.keys_in);
+    K* keys_out = static_cast<K*>(a.keys_out);
+
+    for (int i = tid; i < WARPS * bins; i += THREADS) {
+        s_cnt[i] = 0;
+        s_match[i] = 0;
+    }
+    for (int d = tid; d < bins; d += THREADS) s_run[d] = a.chunk_off[(size_t)blockIdx.x * bins + d];
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    auto full_bulk_tile = [&](uint32_t t) -> bool { return a.use_bulk && (size_t)(t + 1) * TILE <= a.n; };
+    auto issue_tile = [&](uint32_t t, int b) {
+        unsigned char* dst = buf0 + (size_t)b * Cfg::kBufBytes;
+        constexpr uint32_t kb = TILE * sizeof(K);
+        constexpr uint32_t vb = VALS ? TILE * 4 : 0;
+        mbar_arrive_expect_tx(&bars[b], kb + vb);
+        bulk_load(dst, keys_in + (size_t)t * TILE, kb, &bars[b]);
+        if constexpr (VALS) bulk_load(dst + kb, a.vals_in + (size_t)t * TILE, vb, &bars[b]);
+    };
+    if (tid == 0 && full_bulk_tile(t_begin)) issue_tile(t_begin, 0);
+    uint32_t phase = 0u;
+    int b = 0;
+    for (uint32_t tile = t_begin; tile < t_end; ++tile, b ^= 1) {
+        if (tid == 0 && tile + 1 < t_end && full_bulk_tile(tile + 1)) {
+            fence_proxy_async_smem();
+            issue_tile(tile + 1, b ^ 1);
+        }
+        K* s_keys = reinterpret_cast<K*>(buf0 + (size_t)b * Cfg::kBufBytes);
+        uint32_t* s_vals = reinterpret_cast<uint32_t*>(buf0 + (size_t)b * Cfg::kBufBytes + (size_t)TILE * sizeof(K));
+        const uint32_t tile_base = tile * (uint32_t)TILE;
+        const uint32_t tile_n = min((uint32_t)TILE, a.n - tile_base);
+        bool ok = true;
+        if (full_bulk_tile(tile)) {
+            ok = mbar_wait_bounded(&bars[b], (phase >> b) & 1u, a.limit_ns);
+            phase ^= 1u << b;
+        } else {
+            for (uint32_t j = tid; j < tile_n; j += THREADS) {
+                s_keys[j] = keys_in[tile_base + j];
+                if constexpr (VALS) s_vals[j] = a.vals_in[tile_base + j];
+            }
+        }
+        if (__syncthreads_or(!ok)) {
+            // a bulk copy never completed: record it, wait (bounded) for the
+            // copy issued into the other buffer, and stop
+            if (tid == 0) set_status(a.status, kStatTimeout);
+            if (tile + 1 < t_end && full_bulk_tile(tile + 1))
+                mbar_wait_bounded(&bars[b ^ 1], (phase >> (b ^ 1)) & 1u, a.limit_ns);
+            return;
+        }
+        if (tile_n == (uint32_t)TILE)
+            sweep_tile<K, VALS, THREADS, ITEMS, WIDTH, true>(a, s_keys, s_vals, s_cnt, s_match, s_start, s_tot,
+                                                             s_run, s_delta, s_warp_scan, TILE);
+        else
+            sweep_tile<K, VALS, THREADS, ITEMS, WIDTH, false>(a, s_keys, s_vals, s_cnt, s_match, s_start, s_tot,
+                                                              s_run, s_delta, s_warp_scan, tile_n);
+    }
+}
+
+// ----------------------------------------------------------------------------
 // Host side
 // ----------------------------------------------------------------------------
 namespace {
 
 // Launch shapes of a round (threads x keys per thread).
-constexpr int kShapeThreads[] = {512, 256, 256, 128, 512, 1024};
-constexpr int kShapeItems[] = {8, 16, 8, 16, 16, 8};
+// 0-5: persistent bulk-copy kernel; 6-9: one CTA per tile.
+constexpr int kShapeThreads[] = {512, 256, 256, 128, 512, 1024, 256, 256, 384, 512, 512, 1024, 256};
+constexpr int kShapeItems[] = {8, 16, 8, 16, 16, 8, 16, 12, 12, 8, 16, 16, 32};
 
 int shape_tile(int sh) { return kShapeThreads[sh] * kShapeItems[sh]; }
 
@@ -600,6 +1189,18 @@ isort_status launch_round(PassArgs a, cudaStream_t s) {
     return from_cuda(cudaGetLastError());
 }
 
+template <typename K, bool VALS, int THREADS, int ITEMS, int RANK>
+isort_status launch_round_direct(PassArgs a, cudaStream_t s) {
+    using Cfg = DirectCfg<K, VALS, THREADS, ITEMS>;
+    auto kern = k_onesweep_direct<K, VALS, THREADS, ITEMS, RANK>;
+    const size_t smem = Cfg::smem_bytes(a.bins);
+    if (smem > max_smem_optin()) return ISORT_ERR_UNSUPPORTED;
+    ISORT_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LaunchScope ls("onesweep", s);
+    kern<<<a.num_tiles, THREADS, smem, s>>>(a);
+    return from_cuda(cudaGetLastError());
+}
+
 template <typename K, bool VALS, int RANK>
 isort_status launch_round_shape(int sh, PassArgs a, cudaStream_t s) {
     switch (sh) {
@@ -608,7 +1209,14 @@ isort_status launch_round_shape(int sh, PassArgs a, cudaStream_t s) {
         case 2: return launch_round<K, VALS, 256, 8, RANK>(a, s);
         case 3: return launch_round<K, VALS, 128, 16, RANK>(a, s);
         case 4: return launch_round<K, VALS, 512, 16, RANK>(a, s);
-        default: return launch_round<K, VALS, 1024, 8, RANK>(a, s);
+        case 5: return launch_round<K, VALS, 1024, 8, RANK>(a, s);
+        case 6: return launch_round_direct<K, VALS, 256, 16, RANK>(a, s);
+        case 7: return launch_round_direct<K, VALS, 256, 12, RANK>(a, s);
+        case 8: return launch_round_direct<K, VALS, 384, 12, RANK>(a, s);
+        case 9: return launch_round_direct<K, VALS, 512, 8, RANK>(a, s);
+        case 10: return launch_round_direct<K, VALS, 512, 16, RANK>(a, s);
+        case 11: return launch_round_direct<K, VALS, 1024, 16, RANK>(a, s);
+        default: return launch_round_direct<K, VALS, 256, 32, RANK>(a, s);
     }
 }
 
@@ -617,6 +1225,58 @@ isort_status launch_round_dispatch(int sh, bool vals, PassArgs a, cudaStream_t s
     const int rank = tune().rank_mode;
     if (vals) return rank ? launch_round_shape<K, true, 1>(sh, a, s) : launch_round_shape<K, true, 0>(sh, a, s);
     return rank ? launch_round_shape<K, false, 1>(sh, a, s) : launch_round_shape<K, false, 0>(sh, a, s);
+}
+
+// ---- chunked reduce-then-scan rounds
+constexpr int kSweepThreads[] = {256, 512, 256, 512};
+constexpr int kSweepItems[] = {16, 16, 8, 8};
+
+int sweep_tile(int sh) { return kSweepThreads[sh] * kSweepItems[sh]; }
+
+template <typename K, bool VALS, int THREADS, int ITEMS>
+isort_status sweep_occupancy(int bins, int* per_sm) {
+    using Cfg = SweepCfg<K, VALS, THREADS, ITEMS>;
+    const size_t smem = Cfg::smem_bytes(bins);
+    if (smem > max_smem_optin()) return ISORT_ERR_UNSUPPORTED;
+    auto k8 = k_downsweep<K, VALS, THREADS, ITEMS, 8>;
+    auto k0 = k_downsweep<K, VALS, THREADS, ITEMS, 0>;
+    ISORT_TRY_CUDA(cudaFuncSetAttribute(k8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ISORT_TRY_CUDA(cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int p8 = 0, p0 = 0;
+    ISORT_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p8, k8, THREADS, smem));
+    ISORT_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p0, k0, THREADS, smem));
+    *per_sm = std::min(p8, p0);
+    return *per_sm >= 1 ? ISORT_OK : ISORT_ERR_UNSUPPORTED;
+}
+
+template <typename K, bool VALS, int THREADS, int ITEMS>
+isort_status launch_sweep(const SweepArgs& a, uint32_t chunks, cudaStream_t s) {
+    using Cfg = SweepCfg<K, VALS, THREADS, ITEMS>;
+    LaunchScope ls("downsweep", s);
+    if (a.width == 8)
+        k_downsweep<K, VALS, THREADS, ITEMS, 8><<<chunks, THREADS, Cfg::smem_bytes(a.bins), s>>>(a);
+    else
+        k_downsweep<K, VALS, THREADS, ITEMS, 0><<<chunks, THREADS, Cfg::smem_bytes(a.bins), s>>>(a);
+    return from_cuda(cudaGetLastError());
+}
+
+template <typename K, bool VALS>
+isort_status sweep_dispatch(int sh, bool occupancy_only, int bins, int* per_sm, const SweepArgs* a, uint32_t chunks,
+                            cudaStream_t s) {
+    switch (sh) {
+        case 0:
+            return occupancy_only ? sweep_occupancy<K, VALS, 256, 16>(bins, per_sm)
+                                  : launch_sweep<K, VALS, 256, 16>(*a, chunks, s);
+        case 1:
+            return occupancy_only ? sweep_occupancy<K, VALS, 512, 16>(bins, per_sm)
+                                  : launch_sweep<K, VALS, 512, 16>(*a, chunks, s);
+        case 2:
+            return occupancy_only ? sweep_occupancy<K, VALS, 256, 8>(bins, per_sm)
+                                  : launch_sweep<K, VALS, 256, 8>(*a, chunks, s);
+        default:
+            return occupancy_only ? sweep_occupancy<K, VALS, 512, 8>(bins, per_sm)
+                                  : launch_sweep<K, VALS, 512, 8>(*a, chunks, s);
+    }
 }
 
 template <typename K>
@@ -637,7 +1297,18 @@ isort_status launch_hist(const K* keys, size_t n, int shift0, int rb, int key_bi
     const int bins = 1 << rb;
     const size_t smem = kHistStages * kHistChunkBytes + align_up((size_t)rounds * bins * 4, 8) + kHistStages * 8;
     if (smem > max_smem_optin()) return ISORT_ERR_UNSUPPORTED;
-    auto kern = tune().hist_agg ? k_digit_hist<K, true> : k_digit_hist<K, false>;
+    void (*kern)(HistArgs) = tune().hist_agg ? k_digit_hist<K, true> : k_digit_hist<K, false>;
+    if (shift0 == 0 && !tune().hist_agg) {
+        if constexpr (sizeof(K) == 4) {
+            if (rb == 8 && key_bits == 32) kern = k_digit_hist<K, false, 8, 32>;
+            else if (rb == 11 && key_bits == 32) kern = k_digit_hist<K, false, 11, 32>;
+            else if (rb == 8 && key_bits == 20) kern = k_digit_hist<K, false, 8, 20>;
+            else if (rb == 11 && key_bits == 20) kern = k_digit_hist<K, false, 11, 20>;
+        } else {
+            if (rb == 8 && key_bits == 64) kern = k_digit_hist<K, false, 8, 64>;
+            else if (rb == 8 && key_bits == 48) kern = k_digit_hist<K, false, 8, 48>;
+        }
+    }
     ISORT_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     ISORT_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kHistThreads, smem));
@@ -696,6 +1367,128 @@ bool valid_widths(int key_width, int& key_bits, int rb) {
     return key_bits >= 1 && key_bits <= key_width && rb >= 1 && rb <= 16;
 }
 
+// The same sort by chunked reduce-then-scan rounds (see k_downsweep).
+template <typename K>
+isort_status radix_device_rts(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n, int key_bits,
+                              int rb, cudaStream_t s) {
+    const int key_width = (int)sizeof(K) * 8;
+    const int rounds = (key_bits + rb - 1) / rb;
+    const int bins = 1 << rb;
+    const bool vals = vin != nullptr;
+    const bool inplace = (const void*)kin == (const void*)kout;
+    const int sh = bins <= 256 ? tune().sweep_small : tune().sweep_large;
+    int per_sm = 0;
+    isort_status st = vals ? sweep_dispatch<K, true>(sh, true, bins, &per_sm, nullptr, 0, s)
+                           : sweep_dispatch<K, false>(sh, true, bins, &per_sm, nullptr, 0, s);
+    if (st != ISORT_OK) return st;
+    const uint32_t tile = (uint32_t)sweep_tile(sh);
+    const uint32_t num_tiles = (uint32_t)((n + tile - 1) / tile);
+    const uint32_t want = (uint32_t)per_sm * (uint32_t)sm_count();
+    const uint32_t chunk_tiles = (num_tiles + want - 1) / want;
+    const uint32_t chunks = (num_tiles + chunk_tiles - 1) / chunk_tiles;
+    const int nsub = bins <= 256 ? 16 : (bins <= 1024 ? 4 : 1);
+
+    int nbuf;
+    if (inplace) nbuf = (rounds % 2 == 0) ? 1 : (rounds == 1 ? 1 : 2);
+    else nbuf = rounds == 1 ? 0 : 1;
+    const size_t buf_bytes = align_up(n * sizeof(K), 256) + (vals ? align_up(n * 4, 256) : 0);
+    const size_t ctl = 256 + 2 * align_up((size_t)chunks * bins * 4, 256);
+    unsigned char* ws = nullptr;
+    st = scratch_alloc((void**)&ws, ctl + (size_t)nbuf * buf_bytes, s);
+    if (st != ISORT_OK) return st;
+    uint32_t* status = reinterpret_cast<uint32_t*>(ws);
+    unsigned long long* key_or = reinterpret_cast<unsigned long long*>(ws + 8);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(ws + 256);
+    uint32_t* coff = reinterpret_cast<uint32_t*>(ws + 256 + align_up((size_t)chunks * bins * 4, 256));
+    K* wk[2] = {nullptr, nullptr};
+    uint32_t* wv[2] = {nullptr, nullptr};
+    for (int i = 0; i < nbuf; ++i) {
+        unsigned char* p = ws + ctl + (size_t)i * buf_bytes;
+        wk[i] = reinterpret_cast<K*>(p);
+        wv[i] = vals ? reinterpret_cast<uint32_t*>(p + align_up(n * sizeof(K), 256)) : nullptr;
+    }
+    auto fail = [&](isort_status e) {
+        scratch_free(ws, s);
+        return e;
+    };
+    cudaError_t ce = cudaMemsetAsync(ws, 0, 256, s);
+    if (ce != cudaSuccess) return fail(from_cuda(ce));
+    const size_t hist_smem = (size_t)nsub * bins * 4;
+    ce = cudaFuncSetAttribute(k_chunk_hist<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hist_smem);
+    if (ce != cudaSuccess) return fail(from_cuda(ce));
+    const K* src_k = kin;
+    const uint32_t* src_v = vin;
+    for (int d = 0; d < rounds; ++d) {
+        K* dk;
+        uint32_t* dv;
+        if (!inplace) {
+            const bool to_out = ((rounds - 1 - d) % 2) == 0;
+            dk = to_out ? kout : wk[0];
+            dv = to_out ? vout : wv[0];
+        } else if (rounds == 1) {
+            dk = wk[0];
+            dv = wv[0];
+        } else if (rounds % 2 == 0) {
+            const bool to_out = (d % 2) == 1;
+            dk = to_out ? kout : wk[0];
+            dv = to_out ? vout : wv[0];
+        } else if (d == rounds - 1) {
+            dk = kout;
+            dv = vout;
+        } else {
+            dk = wk[d % 2];
+            dv = wv[d % 2];
+        }
+        const int shift = d * rb;
+        const int width = std::min(rb, key_bits - shift);
+        {
+            LaunchScope ls("chunk_hist", s);
+            k_chunk_hist<K><<<chunks, kChunkHistThreads, hist_smem, s>>>(src_k, (uint32_t)n, shift, width,
+                                                                         chunk_tiles * tile, nsub, hist,
+                                                                         d == 0 ? key_or : nullptr);
+            ce = cudaGetLastError();
+            if (ce != cudaSuccess) return fail(from_cuda(ce));
+        }
+        {
+            LaunchScope ls("chunk_scan", s);
+            const int sbins = 1 << width;
+            const int groups = sbins >= kChunkScanThreads ? 1 : kChunkScanThreads / sbins;
+            k_chunk_scan<<<1, kChunkScanThreads, (size_t)(groups + 1) * sbins * 4, s>>>(
+                hist, (int)chunks, 1 << width, coff, d == 0 ? key_or : nullptr, key_bits, key_width, status);
+            ce = cudaGetLastError();
+            if (ce != cudaSuccess) return fail(from_cuda(ce));
+        }
+        SweepArgs a;
+        a.keys_in = src_k;
+        a.vals_in = src_v;
+        a.keys_out = dk;
+        a.vals_out = dv;
+        a.n = (uint32_t)n;
+        a.shift = shift;
+        a.width = width;
+        a.bins = 1 << width;
+        a.chunk_off = coff;
+        a.chunk_tiles = chunk_tiles;
+        a.num_tiles = num_tiles;
+        a.status = status;
+        a.limit_ns = spin_limit_ns();
+        a.use_bulk = (((uintptr_t)src_k % 16) == 0) && (!vals || ((uintptr_t)src_v % 16) == 0);
+        st = vals ? sweep_dispatch<K, true>(sh, false, a.bins, &per_sm, &a, chunks, s)
+                  : sweep_dispatch<K, false>(sh, false, a.bins, &per_sm, &a, chunks, s);
+        if (st != ISORT_OK) return fail(st);
+        src_k = dk;
+        src_v = dv;
+    }
+    if (inplace && rounds == 1) {
+        ce = cudaMemcpyAsync(kout, wk[0], n * sizeof(K), cudaMemcpyDeviceToDevice, s);
+        if (ce == cudaSuccess && vals) ce = cudaMemcpyAsync(vout, wv[0], n * 4, cudaMemcpyDeviceToDevice, s);
+        if (ce != cudaSuccess) return fail(from_cuda(ce));
+    }
+    st = finish_status(status, s);
+    scratch_free(ws, s);
+    return st;
+}
+
 // Sorts device buffers. kin/vin are read; the result lands in kout/vout.
 // If kin == kout the sort is in place (vin == vout then too).
 template <typename K>
@@ -705,6 +1498,12 @@ isort_status radix_device(const K* kin, const uint32_t* vin, K* kout, uint32_t* 
     const int rounds = (key_bits + rb - 1) / rb;
     const int bins = 1 << rb;
     if (rb > 12) return ISORT_ERR_UNSUPPORTED;
+    if (tune().algo == 1 && peek_stall_tile() < 0) {
+        // chunked rounds; wide digits whose tables do not fit on chip take
+        // the single-pass rounds below (refused before any work is enqueued)
+        const isort_status st = radix_device_rts<K>(kin, vin, kout, vout, n, key_bits, rb, s);
+        if (st != ISORT_ERR_UNSUPPORTED) return st;
+    }
     const bool vals = vin != nullptr;
     const bool inplace = (const void*)kin == (const void*)kout;
     const int sh = bins <= 256 ? tune().shape_small : tune().shape_large;

@@ -70,8 +70,15 @@ __global__ void k_fold_status(const uint32_t* st) {
     }
 }
 
+thread_local char t_last_error[160] = "";
+
+static void note_error(const char* what) {
+    std::snprintf(t_last_error, sizeof(t_last_error), "%s", what);
+}
+
 isort_status from_cuda(cudaError_t e) {
     if (e == cudaSuccess) return ISORT_OK;
+    note_error(cudaGetErrorString(e));
     if (e == cudaErrorMemoryAllocation) {
         cudaGetLastError();
         return ISORT_ERR_NO_MEMORY;
@@ -118,8 +125,14 @@ size_t max_smem_optin() {
 bool sync_mode() { return g_sync.load() != 0; }
 uint64_t spin_limit_ns() { return g_spin_ns.load(); }
 int64_t take_stall_tile() { return g_stall.exchange(-1); }
+int64_t peek_stall_tile() { return g_stall.load(); }
 
 static isort_status map_bits(uint32_t v) {
+    if (v) {
+        char buf[96];
+        std::snprintf(buf, sizeof(buf), "device status bits 0x%x (1 key range, 2 timeout, 4 output index, 8 offsets)", v);
+        note_error(buf);
+    }
     if (v & kStatTimeout) return ISORT_ERR_TIMEOUT;
     if (v & kStatBadOffsets) return ISORT_ERR_INVALID_ARG;
     if (v & kStatUnsupported) return ISORT_ERR_UNSUPPORTED;
@@ -230,6 +243,8 @@ isort_status isort_debug_stall_tile(int64_t tile) {
 }
 
 uint64_t isort_launch_count(void) { return g_launches.load(); }
+
+const char* isort_last_error_string(void) { return t_last_error; }
 
 isort_status isort_profile_enable(int on) {
     g_profile.store(on ? 1 : 0);

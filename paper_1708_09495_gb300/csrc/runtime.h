@@ -6,7 +6,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
-#include "../../include/isort.h"
+#include "isort.h"
 
 namespace isort {
 
@@ -19,6 +19,7 @@ size_t max_smem_optin();        // opt-in dynamic shared memory per block
 bool sync_mode();
 uint64_t spin_limit_ns();
 int64_t take_stall_tile();      // consumes the injected stall (-1 if none)
+int64_t peek_stall_tile();      // the injected stall without consuming it
 
 // Finishes a call whose kernels recorded device errors into d_status:
 // in synchronous mode waits for `s` and maps the bits to a status; in

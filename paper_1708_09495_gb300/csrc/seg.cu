@@ -159,6 +159,12 @@ __global__ void __launch_bounds__(kSegThreads, 2) k_seg_cluster(ClusterArgs a) {
     uint32_t* s_pre = s_cta + kSegBins;                                            // earlier CTAs' counts
     uint32_t* s_base = s_pre + kSegBins;                                           // digit start + s_pre
     uint32_t* s_misc = s_base + kSegBins;  // [0] work item, [1] range flag, [8..] warp sums
+    // (the launch always provides cluster_smem_bytes; every CTA of a cluster
+    // sees the same size, so a failed check leaves the cluster together)
+    if ((size_t)(reinterpret_cast<unsigned char*>(s_misc + 64) - smem) > dynamic_smem_size()) {
+        if (threadIdx.x == 0) set_status(&a.ctl->status, kStatBounds);
+        return;
+    }
 
     cg::cluster_group cluster = cg::this_cluster();
     const uint32_t r = C == 1 ? 0u : cluster.block_rank();
