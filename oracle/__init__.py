@@ -67,6 +67,18 @@ def _lib(mutant: int = 0):
             for nm in ("oracle_multiset_hash_u32", "oracle_multiset_hash_u64"):
                 getattr(h, nm).argtypes = [vp, vp, sz]
                 getattr(h, nm).restype = u64
+            h.oracle_sample_indices.argtypes = [u64, ctypes.c_uint32, u64, vp]
+            h.oracle_sample_indices.restype = None
+            h.oracle_pwl_eval_f32.argtypes = [vp, vp, ctypes.c_float]
+            h.oracle_pwl_eval_f32.restype = ctypes.c_float
+            h.oracle_splitters.argtypes = [vp, vp, i32, i32, i32, vp]
+            h.oracle_splitters.restype = None
+            h.oracle_bucket_ids.argtypes = [vp, i32, sz, vp, i32, vp]
+            h.oracle_bucket_ids.restype = None
+            h.oracle_cdf_knots.argtypes = [vp, vp, vp]
+            h.oracle_cdf_knots.restype = None
+            h.oracle_cdf_loss_grad.argtypes = [vp, ctypes.c_uint32, vp, vp]
+            h.oracle_cdf_loss_grad.restype = ctypes.c_double
             _handles[mutant] = h
     return h
 
@@ -186,3 +198,57 @@ def key_range_ok(keys, key_bits: int) -> bool:
     if key_bits in (0, width):
         return True
     return bool(k.size == 0 or int(k.max()) >> key_bits == 0)
+
+
+# ----------------------------------------------------------------------------- learned buckets
+
+SAMPLE_SEED = 0x5EED5EED5EED
+SAMPLE_SIZE = 1 << 16
+
+
+def sample_indices(n: int, m: int = SAMPLE_SIZE, seed: int = SAMPLE_SEED):
+    """index_j = floor(r_j * n / 2^64), r_j = SplitMix64 output j from state seed."""
+    idx = np.empty(m, np.uint64)
+    _lib().oracle_sample_indices(n, m, seed, _p(idx))
+    return idx
+
+
+def pwl_eval_f32(X, Y, u: float) -> float:
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    Y = np.ascontiguousarray(Y, dtype=np.float32)
+    return float(_lib().oracle_pwl_eval_f32(_p(X), _p(Y), float(np.float32(u))))
+
+
+def splitters(X, Y, key_width: int = 32, key_bits: int = 32, nbuckets: int = 4096):
+    """The splitter table (uint64, nbuckets entries; entry 0 is 0)."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    Y = np.ascontiguousarray(Y, dtype=np.float32)
+    s = np.zeros(nbuckets, np.uint64)
+    _lib().oracle_splitters(_p(X), _p(Y), key_width, key_bits, nbuckets, _p(s))
+    return s
+
+
+def bucket_ids(keys, split):
+    k = np.ascontiguousarray(keys)
+    w = 32 if k.dtype == np.uint32 else 64
+    s = np.ascontiguousarray(split, dtype=np.uint64)
+    ids = np.empty(k.size, np.uint32)
+    _lib().oracle_bucket_ids(_p(k), w, k.size, _p(s), s.size, _p(ids))
+    return ids
+
+
+def cdf_knots(theta):
+    t = np.ascontiguousarray(theta, dtype=np.float64)
+    X = np.empty(257, np.float64)
+    Y = np.empty(257, np.float64)
+    _lib().oracle_cdf_knots(_p(t), _p(X), _p(Y))
+    return X, Y
+
+
+def cdf_loss_grad(u, theta, with_grad: bool = True):
+    """(loss, dloss/dtheta) of the CDF model in double precision."""
+    uu = np.ascontiguousarray(u, dtype=np.float64)
+    t = np.ascontiguousarray(theta, dtype=np.float64)
+    g = np.zeros(512, np.float64) if with_grad else None
+    loss = _lib().oracle_cdf_loss_grad(_p(uu), uu.size, _p(t), _p(g))
+    return float(loss), g

@@ -348,3 +348,156 @@ uint64_t oracle_multiset_hash_u64(const uint64_t* k, const uint32_t* v, size_t n
     for (size_t i = 0; i < n; ++i) h += fmix(k[i] ^ rotl32(v ? (uint64_t)v[i] : 0));
     return h;
 }
+
+/* ------------------------------------------------------------------------
+ * Learned-bucket sort (no counterpart in the paper; its output is still the
+ * stable sort above). These restate the model's definitions for checking.
+ * ---------------------------------------------------------------------- */
+#include <math.h>
+
+#define PWL_SEG 256
+#define PWL_KNOTS 257
+
+/* Sample indices: index_j = floor(r_j * n / 2^64), r_j the j-th output of
+ * SplitMix64 (Steele, Lea & Flood 2014) started from state seed. */
+static uint64_t sm_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+void oracle_sample_indices(uint64_t n, uint32_t m, uint64_t seed, uint64_t* idx) {
+    for (uint32_t j = 0; j < m; ++j) {
+        uint64_t r = sm_mix(seed + (uint64_t)(j + 1) * 0x9E3779B97F4A7C15ULL);
+        idx[j] = (uint64_t)(((unsigned __int128)r * n) >> 64);
+    }
+}
+
+/* F(u) in float, every operation rounded to nearest in this order:
+ * j = the largest j < 256 with X[j] <= u; w = (u - X[j]) / (X[j+1] - X[j]);
+ * F = Y[j] + (Y[j+1] - Y[j]) * w, clamped to [0, 1]; u >= X[256] gives Y[256]. */
+static float pwl_eval_f32(const float* X, const float* Y, float u) {
+    if (!(u < X[PWL_SEG])) return Y[PWL_SEG];
+    int lo = 0, hi = PWL_SEG;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) / 2;
+        if (X[mid] <= u) lo = mid;
+        else hi = mid;
+    }
+    float dx = X[lo + 1] - X[lo];
+    float w = dx > 0.f ? (u - X[lo]) / dx : 0.f;
+    float f = Y[lo] + (Y[lo + 1] - Y[lo]) * w;
+    return f < 0.f ? 0.f : (f > 1.f ? 1.f : f);
+}
+
+float oracle_pwl_eval_f32(const float* X, const float* Y, float u) { return pwl_eval_f32(X, Y, u); }
+
+static float norm_key(uint64_t k, int key_width, float scale) {
+    float fk = key_width == 32 ? (float)(uint32_t)k : (float)k;
+    return fk * scale;
+}
+
+/* Splitter table: s_0 = 0; for b = 1..B-1, s_b = the first key in [0, 2^kb)
+ * with F(key * 2^-kb) >= b/B (the largest key if none), found by bisection;
+ * then s_b = max(s_b, s_{b-1}). */
+void oracle_splitters(const float* X, const float* Y, int key_width, int key_bits, int B, uint64_t* s) {
+    float scale = ldexpf(1.0f, -key_bits);
+    s[0] = 0;
+    for (int b = 1; b < B; ++b) {
+        float target = (float)b / (float)B;
+        uint64_t lo = 0, hi = key_bits >= 64 ? ~0ULL : ((1ULL << key_bits) - 1ULL);
+        while (lo < hi) {
+            uint64_t mid = lo + ((hi - lo) >> 1);
+            if (pwl_eval_f32(X, Y, norm_key(mid, key_width, scale)) >= target) hi = mid;
+            else lo = mid + 1;
+        }
+        s[b] = lo;
+    }
+    for (int b = 1; b < B; ++b)
+        if (s[b] < s[b - 1]) s[b] = s[b - 1];
+}
+
+/* bucket(key) = #{b in 1..B-1 : s_b <= key}. */
+void oracle_bucket_ids(const void* keys, int key_width, size_t n, const uint64_t* s, int B, uint32_t* ids) {
+    for (size_t i = 0; i < n; ++i) {
+        uint64_t k = key_width == 32 ? (uint64_t)((const uint32_t*)keys)[i] : ((const uint64_t*)keys)[i];
+        /* s_1..s_{B-1} is non-decreasing: count the entries <= k by bisection */
+        int lo = 1, hi = B; /* first index in [1, B) with s > k, or B */
+        while (lo < hi) {
+            int mid = (lo + hi) / 2;
+            if (s[mid] <= k) lo = mid + 1;
+            else hi = mid;
+        }
+        ids[i] = (uint32_t)(lo - 1);
+    }
+}
+
+/* The model's knots from theta (double): V_j = sum_{i<j} sp(theta_i) / sum_i sp(theta_i),
+ * sp = softplus; theta[0..255] -> X, theta[256..511] -> Y. */
+static double softplus_d(double t) { return t > 30.0 ? t : log1p(exp(t)); }
+
+void oracle_cdf_knots(const double* theta, double* X, double* Y) {
+    for (int which = 0; which < 2; ++which) {
+        double* V = which == 0 ? X : Y;
+        double S = 0.0;
+        for (int i = 0; i < PWL_SEG; ++i) S += softplus_d(theta[which * PWL_SEG + i]);
+        double run = 0.0;
+        V[0] = 0.0;
+        for (int j = 1; j < PWL_SEG; ++j) {
+            run += softplus_d(theta[which * PWL_SEG + j - 1]);
+            V[j] = run / S;
+        }
+        V[PWL_SEG] = 1.0;
+    }
+}
+
+/* Loss L = (1/m) sum_i (F(u_i) - (i + 1/2)/m)^2 over sorted sample values u,
+ * and its gradient with respect to theta (grad may be NULL), in double. The
+ * gradient is the chain rule written out: dF/dY_j, dF/dX_j from the segment
+ * formula, then dV_j/dtheta_i = sp'(theta_i) (1[i < j] - V_j) / S. */
+double oracle_cdf_loss_grad(const double* u, uint32_t m, const double* theta, double* grad) {
+    double X[PWL_KNOTS], Y[PWL_KNOTS], gX[PWL_KNOTS], gY[PWL_KNOTS];
+    oracle_cdf_knots(theta, X, Y);
+    for (int j = 0; j < PWL_KNOTS; ++j) gX[j] = gY[j] = 0.0;
+    double loss = 0.0;
+    for (uint32_t i = 0; i < m; ++i) {
+        double x = u[i];
+        int j = PWL_SEG - 1;
+        if (x < X[PWL_SEG]) {
+            j = 0;
+            while (j + 1 < PWL_SEG && X[j + 1] <= x) ++j;
+        }
+        double dx = X[j + 1] - X[j], dy = Y[j + 1] - Y[j];
+        double w = dx > 0 ? (x - X[j]) / dx : 0.0;
+        if (w < 0) w = 0;
+        if (w > 1) w = 1;
+        double f = Y[j] + dy * w;
+        double e = f - ((double)i + 0.5) / m;
+        loss += e * e / m;
+        double ge = 2.0 * e / m;
+        gY[j] += ge * (1.0 - w);
+        gY[j + 1] += ge * w;
+        if (dx > 0 && x < X[j + 1]) {
+            double k = ge * dy / (dx * dx);
+            gX[j] += k * (x - X[j + 1]);
+            gX[j + 1] += -k * (x - X[j]);
+        }
+    }
+    if (grad) {
+        for (int which = 0; which < 2; ++which) {
+            const double* V = which == 0 ? X : Y;
+            const double* g = which == 0 ? gX : gY;
+            double S = 0.0, A = 0.0;
+            for (int i = 0; i < PWL_SEG; ++i) S += softplus_d(theta[which * PWL_SEG + i]);
+            for (int j = 0; j < PWL_KNOTS; ++j) A += g[j] * V[j];
+            for (int i = 0; i < PWL_SEG; ++i) {
+                double suffix = 0.0;
+                for (int j = i + 1; j < PWL_KNOTS; ++j) suffix += g[j];
+                double t = theta[which * PWL_SEG + i];
+                double sig = 1.0 / (1.0 + exp(-t));
+                grad[which * PWL_SEG + i] = sig / S * (suffix - A);
+            }
+        }
+    }
+    return loss;
+}
