@@ -153,6 +153,76 @@ ISORT_API isort_status isort_segmented(uint32_t* keys, uint32_t* vals, const uin
                                        int key_bits, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Learned-bucket sort. The paper has no counterpart; it grows out of the
+ * splitter-based sample sorts the paper discusses (Section 2: oversampling and
+ * regular sampling), with the splitters read off a learned CDF, and finishes
+ * buckets with the count-sort rounds of Section 3. One call:
+ *   1. samples 2^16 keys (indices from SplitMix64 seeded with 0x5EED5EED5EED:
+ *      index_j = floor(r_j * n / 2^64)) and sorts them with the radix rounds;
+ *   2. trains a monotone piecewise-linear CDF F over u = key * 2^-key_bits
+ *      (256 segments; knots X_0..X_256 and values Y_0..Y_256 are normalised
+ *      cumulative sums of softplus(theta), so F is monotone by construction;
+ *      knots start at the sample's quantiles) by 64 Adam steps on
+ *      (1/m) sum_i (F(u_i) - (i + 1/2)/m)^2, on the GPU;
+ *   3. derives an integer splitter table s_1..s_{B-1} (s_b = the first key
+ *      with F(key) >= b/B, then made non-decreasing) and assigns every key the
+ *      bucket #{b : s_b <= key}; the model proposes floor(F(u) B) and the
+ *      splitters confirm or correct it;
+ *   4. distributes the keys stably by bucket and sorts every bucket on chip on
+ *      the bits its key range spans (a bucket of one key value is skipped).
+ * The output is the stable sort of the input, whatever the model learned.
+ * keys (u32), vals (optional) are device memory; nbuckets 2..16384 (0 = 4096);
+ * model 0 = the piecewise-linear CDF (1 = a small MLP: ISORT_ERR_UNSUPPORTED).
+ * n < 2^18 sorts with the plain rounds. If more than half of the keys fall in
+ * buckets beyond the on-chip capacity (65,536 keys) the call sorts with the
+ * plain rounds instead (stats->fell_back_to_lsd = 1); fewer such buckets are
+ * sorted by the plain rounds one at a time. The call synchronizes
+ * (the bucket sizes are read on the host). stats (host, may be NULL) receives
+ * the bucket balance and the training record.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    double imbalance_max_over_mean; /* largest bucket / (n / nbuckets) */
+    double overflow_fraction;       /* keys in buckets over 65,536 keys / n */
+    uint64_t fixups;                /* keys whose proposed bucket the splitters corrected */
+    uint64_t overflow_buckets;      /* buckets over 65,536 keys */
+    int fell_back_to_lsd;           /* 1: sorted by the plain rounds */
+    int train_steps;
+    float train_loss_initial;       /* sample loss before training */
+    float train_loss;               /* sample loss after training */
+    int nbuckets;
+} isort_learned_stats;
+ISORT_API isort_status isort_learned(uint32_t* keys, uint32_t* vals, size_t n, int key_bits, int nbuckets, int model,
+                                     isort_learned_stats* stats, void* stream);
+
+/* The learned path's steps, for callers that drive them and for checking:
+ * isort_cdf_train: trains the model on a sorted sample (device, m u32 keys):
+ *   theta (device, 512 floats: 256 knot increments then 256 value
+ *   increments), X and Y (device, 257 floats each) receive the trained model
+ *   (the parameters with the lowest sample loss seen, the initial ones
+ *   included); losses (device, 66 floats) the loss before each of the 64
+ *   steps, then the loss of the returned model, then the loss at the initial
+ *   parameters.
+ * isort_cdf_loss_grad: loss and d loss / d theta at theta (device, 512) on
+ *   u (device, m normalised sorted sample values); grad (device, 512) and
+ *   loss (device, 1) receive them.
+ * isort_cdf_splitters: the splitter table of step 3 from X, Y (device, 257
+ *   floats each): splitters (device, nbuckets entries of key_width bits,
+ *   nbuckets 2..65536; entry 0 is 0).
+ * isort_bucket_ids: the bucket of every key (device, key_width 32 or 64) given
+ *   X, Y and the splitter table (nbuckets 2..16384); ids (device, n uint32,
+ *   n < 2^32).
+ */
+ISORT_API isort_status isort_cdf_train(const uint32_t* sorted_sample, uint32_t m, int key_bits, float* theta, float* X,
+                                       float* Y, float* losses, void* stream);
+ISORT_API isort_status isort_cdf_loss_grad(const float* u, uint32_t m, const float* theta, float* grad, float* loss,
+                                           void* stream);
+ISORT_API isort_status isort_cdf_splitters(const float* X, const float* Y, int key_width, int key_bits, int nbuckets,
+                                           void* splitters, void* stream);
+ISORT_API isort_status isort_bucket_ids(const void* keys, int key_width, size_t n, int key_bits, const float* X,
+                                        const float* Y, const void* splitters, int nbuckets, uint32_t* ids,
+                                        void* stream);
+
+/* ---------------------------------------------------------------------------
  * isort_radix_noalloc: isort_radix (in place, u32 keys, optional u32 payload)
  * for callers that must not allocate memory. The paper has no counterpart; it
  * exists because some callers cannot let a library allocate device memory:

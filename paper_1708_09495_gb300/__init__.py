@@ -40,6 +40,16 @@ OK, INVALID_ARG, KEY_RANGE, NO_MEMORY, CUDA_ERROR, TIMEOUT, UNSUPPORTED = range(
 _vp, _sz, _i32, _u64, _i64 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint64, ctypes.c_int64
 
 
+class LearnedStats(ctypes.Structure):
+    _fields_ = [("imbalance_max_over_mean", ctypes.c_double), ("overflow_fraction", ctypes.c_double),
+                ("fixups", ctypes.c_uint64), ("overflow_buckets", ctypes.c_uint64),
+                ("fell_back_to_lsd", ctypes.c_int), ("train_steps", ctypes.c_int),
+                ("train_loss_initial", ctypes.c_float), ("train_loss", ctypes.c_float), ("nbuckets", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
 
@@ -59,6 +69,11 @@ SIGNATURES = [
     ("isort_oet_p", _i32, [_vp, _vp, _sz, _i32, _vp, _vp]),
     ("isort_segmented", _i32, [_vp, _vp, _vp, _sz, _i32, _vp]),
     ("isort_radix_noalloc", _i32, [_vp, _vp, _sz, _i32, _i32, _vp]),
+    ("isort_learned", _i32, [_vp, _vp, _sz, _i32, _i32, _i32, _vp, _vp]),
+    ("isort_cdf_train", _i32, [_vp, ctypes.c_uint32, _i32, _vp, _vp, _vp, _vp, _vp]),
+    ("isort_cdf_loss_grad", _i32, [_vp, ctypes.c_uint32, _vp, _vp, _vp, _vp]),
+    ("isort_cdf_splitters", _i32, [_vp, _vp, _i32, _i32, _i32, _vp, _vp]),
+    ("isort_bucket_ids", _i32, [_vp, _i32, _sz, _i32, _vp, _vp, _vp, _i32, _vp, _vp]),
     ("isort_set_sync", _i32, [_i32]),
     ("isort_device_status", _i32, [_i32, _vp]),
     ("isort_set_spin_limit", _i32, [_u64]),
@@ -227,6 +242,59 @@ def segmented(keys, vals, offsets, key_bits: int = 0, stream=None):
     _check(load().isort_segmented(_ptr(keys), _ptr(vals), _ptr(offsets), offsets.numel() - 1, key_bits,
                                   _stream(stream)), "isort_segmented")
     return keys, vals
+
+
+def learned(keys, vals=None, key_bits: int = 0, nbuckets: int = 4096, model: int = 0, stream=None):
+    """Learned-bucket stable sort of uint32 keys (in place). Returns the stats dict."""
+    st = LearnedStats()
+    _check(load().isort_learned(_ptr(keys), _ptr(vals), keys.numel(), key_bits, nbuckets, model, ctypes.byref(st),
+                                _stream(stream)), "isort_learned")
+    return st.as_dict()
+
+
+def cdf_train(sorted_sample, key_bits: int = 32, stream=None):
+    """Trains the CDF model on a sorted uint32 sample; returns (theta, X, Y, losses) tensors."""
+    import torch
+
+    dev = sorted_sample.device
+    theta = torch.empty(512, dtype=torch.float32, device=dev)
+    X = torch.empty(257, dtype=torch.float32, device=dev)
+    Y = torch.empty(257, dtype=torch.float32, device=dev)
+    losses = torch.empty(66, dtype=torch.float32, device=dev)
+    _check(load().isort_cdf_train(_ptr(sorted_sample), sorted_sample.numel(), key_bits, _ptr(theta), _ptr(X), _ptr(Y),
+                                  _ptr(losses), _stream(stream)), "isort_cdf_train")
+    return theta, X, Y, losses
+
+
+def cdf_loss_grad(u, theta, stream=None):
+    """(loss, grad) of the CDF model at theta on normalised sorted sample values u."""
+    import torch
+
+    grad = torch.empty(512, dtype=torch.float32, device=u.device)
+    loss = torch.empty(1, dtype=torch.float32, device=u.device)
+    _check(load().isort_cdf_loss_grad(_ptr(u), u.numel(), _ptr(theta), _ptr(grad), _ptr(loss), _stream(stream)),
+           "isort_cdf_loss_grad")
+    return loss, grad
+
+
+def cdf_splitters(X, Y, key_width: int = 32, key_bits: int = 0, nbuckets: int = 4096, stream=None):
+    import torch
+
+    dt = torch.int32 if key_width == 32 else torch.int64
+    out = torch.empty(nbuckets, dtype=dt, device=X.device)
+    _check(load().isort_cdf_splitters(_ptr(X), _ptr(Y), key_width, key_bits, nbuckets, _ptr(out), _stream(stream)),
+           "isort_cdf_splitters")
+    return out
+
+
+def bucket_ids(keys, X, Y, splitters, key_bits: int = 0, stream=None):
+    import torch
+
+    w = _key_width(keys)
+    ids = torch.empty(keys.numel(), dtype=torch.int32, device=keys.device)
+    _check(load().isort_bucket_ids(_ptr(keys), w, keys.numel(), key_bits, _ptr(X), _ptr(Y), _ptr(splitters),
+                                   splitters.numel(), _ptr(ids), _stream(stream)), "isort_bucket_ids")
+    return ids
 
 
 def set_sync(on: bool):

@@ -127,7 +127,7 @@ uint64_t spin_limit_ns() { return g_spin_ns.load(); }
 int64_t take_stall_tile() { return g_stall.exchange(-1); }
 int64_t peek_stall_tile() { return g_stall.load(); }
 
-static isort_status map_bits(uint32_t v) {
+isort_status map_bits(uint32_t v) {
     if (v) {
         char buf[96];
         std::snprintf(buf, sizeof(buf), "device status bits 0x%x (1 key range, 2 timeout, 4 output index, 8 offsets)", v);

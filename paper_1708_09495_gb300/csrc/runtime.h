@@ -25,6 +25,8 @@ int64_t peek_stall_tile();      // the injected stall without consuming it
 // in synchronous mode waits for `s` and maps the bits to a status; in
 // asynchronous mode folds them into the device's sticky status word.
 isort_status finish_status(const uint32_t* d_status, cudaStream_t s);
+// The status of a device status word already read on the host.
+isort_status map_bits(uint32_t v);
 
 isort_status from_cuda(cudaError_t e);
 

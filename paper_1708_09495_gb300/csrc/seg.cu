@@ -61,7 +61,7 @@ struct SegCtl {
 };
 
 __global__ void k_seg_classify(const uint64_t* off, uint32_t nseg, SegThresholds th, SegCtl* ctl, uint32_t* lists,
-                               int big_ok) {
+                               int big_ok, const uint8_t* seg_bits) {
     for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
         const uint64_t lo = off[s], hi = off[s + 1];
         if (hi < lo) {
@@ -70,6 +70,7 @@ __global__ void k_seg_classify(const uint64_t* off, uint32_t nseg, SegThresholds
         }
         const uint64_t L = hi - lo;
         if (L <= 1) continue;
+        if (seg_bits && seg_bits[s] == 0) continue;  // one key value: already in order
         int c;
         if (L <= th.oet) c = kClsOet;
         else if (L <= th.btn_warp) c = kClsBtnWarp;
@@ -141,6 +142,8 @@ struct ClusterArgs {
     SegCtl* ctl;
     int cls;
     int key_bits;
+    const uint32_t* seg_lo;   // optional: segment s's keys lie in [seg_lo[s], seg_lo[s] + 2^seg_bits[s])
+    const uint8_t* seg_bits;  //   and are sorted on key - seg_lo[s] over seg_bits[s] bits
 };
 
 constexpr size_t cluster_smem_bytes(bool vals) {
@@ -170,7 +173,6 @@ __global__ void __launch_bounds__(kSegThreads, 2) k_seg_cluster(ClusterArgs a) {
     const uint32_t r = C == 1 ? 0u : cluster.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t cnt = a.ctl->counts[a.cls];
-    const int rounds = (a.key_bits + 7) / 8;
 
     for (int i = tid; i < kSegWarps * kSegBins; i += kSegThreads) s_cnt[i] = 0;
 
@@ -182,6 +184,10 @@ __global__ void __launch_bounds__(kSegThreads, 2) k_seg_cluster(ClusterArgs a) {
         const uint32_t s = a.list[q];
         const uint64_t lo = a.off[s];
         const uint32_t L = (uint32_t)(a.off[s + 1] - lo);
+        const uint32_t kbase = a.seg_lo ? a.seg_lo[s] : 0u;
+        const int sbits = a.seg_bits ? (int)a.seg_bits[s] : a.key_bits;
+        const int rounds = (sbits + 7) / 8;
+        const int check_bits = a.seg_bits ? 32 : a.key_bits;
         const uint32_t my_lo = r * (uint32_t)kSegChunk;
         const uint32_t my_n = L > my_lo ? min(L - my_lo, (uint32_t)kSegChunk) : 0u;
         uint32_t* gk = a.keys + lo + my_lo;
@@ -196,7 +202,7 @@ __global__ void __launch_bounds__(kSegThreads, 2) k_seg_cluster(ClusterArgs a) {
             if constexpr (VALS) v[i] = j < my_n ? gv[j] : 0u;
             orv |= k[i];
         }
-        const int bad_local = a.key_bits < 32 && (orv >> a.key_bits) != 0;
+        const int bad_local = check_bits < 32 && (orv >> check_bits) != 0;
         const int bad_cta = __syncthreads_or(bad_local);
         if (tid == 0) s_misc[1] = (uint32_t)bad_cta;
 
@@ -208,7 +214,7 @@ __global__ void __launch_bounds__(kSegThreads, 2) k_seg_cluster(ClusterArgs a) {
             for (int i = 0; i < kSegItems; ++i) {
                 const uint32_t j = (uint32_t)(warp * kSegItems * 32 + i * 32 + lane);
                 const bool valid = j < my_n;
-                const uint32_t dg = (k[i] >> shift) & 0xffu;
+                const uint32_t dg = ((k[i] - kbase) >> shift) & 0xffu;
                 uint32_t peers = __ballot_sync(kFullMask, valid);
 #pragma unroll
                 for (int b = 0; b < 8; ++b) {
@@ -235,7 +241,7 @@ __global__ void __launch_bounds__(kSegThreads, 2) k_seg_cluster(ClusterArgs a) {
                 s_cta[tid] = sum;
             }
             cluster.sync();  // every CTA's digit totals (and range flag) are visible
-            if (d == 0 && a.key_bits < 32) {
+            if (d == 0 && check_bits < 32) {
                 uint32_t any = 0;
                 for (int rr = 0; rr < C; ++rr) any |= C == 1 ? s_misc[1] : *cluster.map_shared_rank(&s_misc[1], rr);
                 if (any) {
@@ -250,7 +256,7 @@ __global__ void __launch_bounds__(kSegThreads, 2) k_seg_cluster(ClusterArgs a) {
                 for (int rr = 0; rr < C; ++rr) {
                     const uint32_t c = C == 1 ? s_cta[tid] : *cluster.map_shared_rank(&s_cta[tid], rr);
                     tot += c;
-                    pre += (uint32_t)rr < r ? c : 0u;
+                    if constexpr (C > 1) pre += (uint32_t)rr < r ? c : 0u;
                 }
                 s_pre[tid] = pre;
                 s_base[tid] = tot;
@@ -280,7 +286,7 @@ __global__ void __launch_bounds__(kSegThreads, 2) k_seg_cluster(ClusterArgs a) {
             for (int i = 0; i < kSegItems; ++i) {
                 const uint32_t j = (uint32_t)(warp * kSegItems * 32 + i * 32 + lane);
                 if (j < my_n) {
-                    const uint32_t dg = (k[i] >> shift) & 0xffu;
+                    const uint32_t dg = ((k[i] - kbase) >> shift) & 0xffu;
                     const uint32_t pos = s_base[dg] + s_cnt[warp * kSegBins + dg] + rank[i];
                     const uint32_t owner = pos >> kSegChunkLog;
                     const uint32_t o = pos & (kSegChunk - 1);
@@ -365,14 +371,15 @@ isort_status launch_cluster(bool vals, const ClusterArgs& a, cudaStream_t s) {
 
 // Enqueues classification and every class kernel on `s`.
 isort_status enqueue_segmented(uint32_t* keys, uint32_t* vals, const uint64_t* off, uint32_t nseg, int key_bits,
-                               SegCtl* ctl, uint32_t* lists, int big_ok, cudaStream_t s) {
+                               SegCtl* ctl, uint32_t* lists, int big_ok, cudaStream_t s,
+                               const uint32_t* seg_lo = nullptr, const uint8_t* seg_bits = nullptr) {
     const SegThresholds th = seg_tune().th;
-    const uint32_t range_mask = key_bits >= 32 ? 0u : ~((1u << key_bits) - 1u);
+    const uint32_t range_mask = (key_bits >= 32 || seg_bits) ? 0u : ~((1u << key_bits) - 1u);
     ISORT_TRY_CUDA(cudaMemsetAsync(ctl, 0, sizeof(SegCtl), s));
     {
         LaunchScope ls("seg_classify", s);
         const unsigned grid = (unsigned)std::max<uint32_t>(1, std::min<uint32_t>((nseg + 255) / 256, 4 * sm_count()));
-        k_seg_classify<<<grid, 256, 0, s>>>(off, nseg, th, ctl, lists, big_ok);
+        k_seg_classify<<<grid, 256, 0, s>>>(off, nseg, th, ctl, lists, big_ok, seg_bits);
         ISORT_TRY_CUDA(cudaGetLastError());
     }
     ClusterArgs a;
@@ -381,6 +388,8 @@ isort_status enqueue_segmented(uint32_t* keys, uint32_t* vals, const uint64_t* o
     a.off = off;
     a.ctl = ctl;
     a.key_bits = key_bits;
+    a.seg_lo = seg_lo;
+    a.seg_bits = seg_bits;
     const bool v = vals != nullptr;
     // largest segments first: they take longest
     const int order[4] = {kClsC8, kClsC4, kClsC2, kClsC1};
@@ -429,7 +438,8 @@ struct GraphCache {
 thread_local GraphCache g_graph;
 
 isort_status launch_via_graph(uint32_t* keys, uint32_t* vals, const uint64_t* off, uint32_t nseg, int key_bits,
-                              SegCtl* ctl, uint32_t* lists, int big_ok, cudaStream_t s) {
+                              SegCtl* ctl, uint32_t* lists, int big_ok, cudaStream_t s,
+                              const uint32_t* seg_lo = nullptr, const uint8_t* seg_bits = nullptr) {
     int dev = 0;
     ISORT_TRY_CUDA(cudaGetDevice(&dev));
     GraphCache& gc = g_graph;
@@ -445,7 +455,7 @@ isort_status launch_via_graph(uint32_t* keys, uint32_t* vals, const uint64_t* of
     isort_status st;
     {
         CaptureScope cs;  // launches are counted, not timed, while capturing
-        st = enqueue_segmented(keys, vals, off, nseg, key_bits, ctl, lists, big_ok, gc.cap);
+        st = enqueue_segmented(keys, vals, off, nseg, key_bits, ctl, lists, big_ok, gc.cap, seg_lo, seg_bits);
     }
     cudaError_t ce = cudaStreamEndCapture(gc.cap, &graph);
     if (st != ISORT_OK) {
@@ -476,7 +486,7 @@ isort_status launch_via_graph(uint32_t* keys, uint32_t* vals, const uint64_t* of
 }
 
 isort_status segmented_entry(uint32_t* keys, uint32_t* vals, const uint64_t* off, size_t nseg, int key_bits,
-                             void* stream) {
+                             void* stream, const uint32_t* seg_lo = nullptr, const uint8_t* seg_bits = nullptr) {
     if (key_bits == 0) key_bits = 32;
     if (key_bits < 1 || key_bits > 32) return ISORT_ERR_INVALID_ARG;
     if (nseg == 0) return ISORT_OK;
@@ -498,9 +508,9 @@ isort_status segmented_entry(uint32_t* keys, uint32_t* vals, const uint64_t* off
     const int big_ok = sync_mode() && cap != cudaStreamCaptureStatusActive;
     if (cap == cudaStreamCaptureStatusActive) {
         // the caller is building its own graph: enqueue directly
-        st = enqueue_segmented(keys, vals, off, ns, key_bits, ctl, lists, big_ok, s);
+        st = enqueue_segmented(keys, vals, off, ns, key_bits, ctl, lists, big_ok, s, seg_lo, seg_bits);
     } else {
-        st = launch_via_graph(keys, vals, off, ns, key_bits, ctl, lists, big_ok, s);
+        st = launch_via_graph(keys, vals, off, ns, key_bits, ctl, lists, big_ok, s, seg_lo, seg_bits);
     }
     if (st != ISORT_OK) {
         scratch_free(ws, s);
@@ -542,6 +552,14 @@ isort_status segmented_entry(uint32_t* keys, uint32_t* vals, const uint64_t* off
 }
 
 }  // namespace
+
+// The finishing step of the learned-bucket sort: every bucket is a segment
+// whose keys lie in [seg_lo[s], seg_lo[s] + 2^seg_bits[s]).
+isort_status segmented_finish_u32(uint32_t* keys, uint32_t* vals, const uint64_t* off, uint32_t nseg,
+                                  const uint32_t* seg_lo, const uint8_t* seg_bits, cudaStream_t s) {
+    return segmented_entry(keys, vals, off, nseg, 32, (void*)s, seg_lo, seg_bits);
+}
+
 }  // namespace isort
 
 using namespace isort;
