@@ -307,6 +307,146 @@ def run_ours(args):
     return 0
 
 
+def _timed_inplace(call, reset, steps, warmup, stream):
+    """Runs reset() then call() per step; times call() alone with CUDA events
+    on the stream; returns the total milliseconds over the timed steps."""
+    import torch
+
+    for _ in range(warmup):
+        reset()
+        call()
+    torch.cuda.synchronize()
+    total = 0.0
+    for _ in range(steps):
+        reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        call()
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    return total
+
+
+def run_compare(args):
+    """Secondary workloads, each against plain LSD on the same data (one GPU):
+    learned: keys-only skewed u32 (n = 2^log2n), learned-bucket sort vs the
+             plain radix rounds;
+    segmented: the log-uniform-length segment batch (2^28 keys, payload),
+             batched segmented sort vs one plain LSD of composite u64 keys
+             (segment id << 32 | key).
+    Inputs are restored from a pristine copy before every step (not timed)."""
+    import numpy as np
+    import torch
+
+    import paper_1708_09495_gb300 as isort
+    from gen import workloads
+
+    lib = isort.load()
+    stream = torch.cuda.current_stream()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    peak, peak_kind = peaks()
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "dtype": "u32", "data": "synthetic"}
+    if args.workload == "learned":
+        n = 1 << args.log2n
+        keys = workloads.skewed(args.dist, n)
+        kin = torch.from_numpy(keys.view(np.int32)).cuda()
+        kw = torch.empty_like(kin)
+        st = isort.LearnedStats()
+
+        def learned():
+            rc = lib.isort_learned(ctypes.c_void_p(kw.data_ptr()), None, n, 32, 0, 0, ctypes.byref(st), sp)
+            if rc != 0:
+                raise RuntimeError(f"isort_learned: {isort.STATUS.get(rc, rc)}")
+
+        def plain():
+            rc = lib.isort_radix(ctypes.c_void_p(kw.data_ptr()), None, n, 32, 8, sp)
+            if rc != 0:
+                raise RuntimeError(f"isort_radix: {isort.STATUS.get(rc, rc)}")
+
+        reset = lambda: kw.copy_(kin)
+        isort.profile_read()
+        isort.profile_enable(True)
+        ms_l = _timed_inplace(learned, reset, args.steps, args.warmup, stream)
+        isort.profile_enable(False)
+        prof = isort.profile_read()
+        sk = kw[:: max(1, n // 4096)].cpu().numpy().view(np.uint32)
+        if not np.all(sk[1:] >= sk[:-1]):
+            raise RuntimeError("learned output not sorted")
+        ms_p = _timed_inplace(plain, reset, args.steps, args.warmup, stream)
+        stats = st.as_dict()
+        value = args.steps * n / (ms_l * 1e-3) / 1e9
+        sw = prof.get("bucket_sweep", (0, 0.0))
+        achieved = n * 8 / (sw[1] / sw[0] * 1e-3) / 1e9 if sw[0] else None
+        line.update({
+            "value": value, "ms_per_step": ms_l / args.steps,
+            "config": {"workload": f"learned-bucket sort, u32 keys-only, {args.dist} (seed 6), n = 2^{args.log2n}",
+                       "l2": "inputs larger than L2; restored before each step (untimed)"},
+            "plain_lsd": {"value": args.steps * n / (ms_p * 1e-3) / 1e9, "ms_per_step": ms_p / args.steps,
+                          "call": "isort_radix, radix 2^8, in place"},
+            "speedup_vs_plain": ms_p / ms_l,
+            "learned_stats": stats,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak if achieved else None, "traffic": None,
+                         "kernel": "bucket_sweep (one stable distribution pass, 8 B/key)", "peak_kind": peak_kind},
+            "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in prof.items()},
+        })
+    else:
+        keys, vals, off = workloads.segmented()
+        n = int(off[-1])
+        nseg = off.size - 1
+        kin = torch.from_numpy(keys.view(np.int32)).cuda()
+        vin = torch.from_numpy(vals.view(np.int32)).cuda()
+        doff = torch.from_numpy(off.view(np.int64)).cuda()
+        kw, vw = torch.empty_like(kin), torch.empty_like(vin)
+        seg_id = np.repeat(np.arange(nseg, dtype=np.uint64), np.diff(off).astype(np.int64))
+        comp = (seg_id << np.uint64(32)) | keys.astype(np.uint64)
+        cin = torch.from_numpy(comp.view(np.int64)).cuda()
+        cw = torch.empty_like(cin)
+        cbits = 32 + int(nseg - 1).bit_length()
+
+        def segmented():
+            rc = lib.isort_segmented(ctypes.c_void_p(kw.data_ptr()), ctypes.c_void_p(vw.data_ptr()),
+                                     ctypes.c_void_p(doff.data_ptr()), nseg, 32, sp)
+            if rc != 0:
+                raise RuntimeError(f"isort_segmented: {isort.STATUS.get(rc, rc)}")
+
+        def composite():
+            rc = lib.isort_radix_u64(ctypes.c_void_p(cw.data_ptr()), ctypes.c_void_p(vw.data_ptr()), n, cbits, 8,
+                                     sp)
+            if rc != 0:
+                raise RuntimeError(f"isort_radix_u64: {isort.STATUS.get(rc, rc)}")
+
+        def reset_s():
+            kw.copy_(kin)
+            vw.copy_(vin)
+
+        def reset_c():
+            cw.copy_(cin)
+            vw.copy_(vin)
+
+        isort.profile_read()
+        isort.profile_enable(True)
+        ms_s = _timed_inplace(segmented, reset_s, args.steps, args.warmup, stream)
+        isort.profile_enable(False)
+        prof = isort.profile_read()
+        ms_c = _timed_inplace(composite, reset_c, args.steps, args.warmup, stream)
+        value = args.steps * n / (ms_s * 1e-3) / 1e9
+        line.update({
+            "value": value, "ms_per_step": ms_s / args.steps,
+            "config": {"workload": f"batched segmented sort, {nseg} segments of log-uniform length in [2, 65536], "
+                                   f"n = {n} u32 keys + u32 payload (seed 4)",
+                       "l2": "inputs larger than L2; restored before each step (untimed)"},
+            "plain_lsd": {"value": args.steps * n / (ms_c * 1e-3) / 1e9, "ms_per_step": ms_c / args.steps,
+                          "call": f"isort_radix_u64 on (segment id << 32 | key), {cbits} key bits, radix 2^8"},
+            "speedup_vs_plain": ms_c / ms_s,
+            "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in prof.items()},
+        })
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -317,12 +457,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--log2n", type=int, default=28)
     ap.add_argument("--radix-bits", type=int, default=8)
+    ap.add_argument("--workload", default="uniform", choices=["uniform", "learned", "segmented"],
+                    help="uniform: the benchmark; learned / segmented: secondary comparisons with plain LSD")
+    ap.add_argument("--dist", default="lognormal", choices=["zipf", "lognormal", "gmm"])
     args = ap.parse_args()
     configure(args)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "uniform":
+        return run_compare(args)
     return run_ours(args)
 
 

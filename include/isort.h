@@ -171,7 +171,8 @@ ISORT_API isort_status isort_segmented(uint32_t* keys, uint32_t* vals, const uin
  *   4. distributes the keys stably by bucket and sorts every bucket on chip on
  *      the bits its key range spans (a bucket of one key value is skipped).
  * The output is the stable sort of the input, whatever the model learned.
- * keys (u32), vals (optional) are device memory; nbuckets 2..16384 (0 = 4096);
+ * keys (u32), vals (optional) are device memory; nbuckets 2..16384 (0 = 4096,
+ * doubled up to 16384 while n / nbuckets > 16,384);
  * model 0 = the piecewise-linear CDF (1 = a small MLP: ISORT_ERR_UNSUPPORTED).
  * n < 2^18 sorts with the plain rounds. If more than half of the keys fall in
  * buckets beyond the on-chip capacity (65,536 keys) the call sorts with the

@@ -244,8 +244,9 @@ def segmented(keys, vals, offsets, key_bits: int = 0, stream=None):
     return keys, vals
 
 
-def learned(keys, vals=None, key_bits: int = 0, nbuckets: int = 4096, model: int = 0, stream=None):
-    """Learned-bucket stable sort of uint32 keys (in place). Returns the stats dict."""
+def learned(keys, vals=None, key_bits: int = 0, nbuckets: int = 0, model: int = 0, stream=None):
+    """Learned-bucket stable sort of uint32 keys (in place). Returns the stats
+    dict. nbuckets 0 lets the library choose (4096 up to 16384 with n)."""
     st = LearnedStats()
     _check(load().isort_learned(_ptr(keys), _ptr(vals), keys.numel(), key_bits, nbuckets, model, ctypes.byref(st),
                                 _stream(stream)), "isort_learned")

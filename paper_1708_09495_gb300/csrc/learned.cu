@@ -14,13 +14,14 @@
 //      Flood 2014), sort them with the library's own radix rounds;
 //   2. train the 256-segment PWL CDF (learned.cuh) by Adam on the mean squared
 //      error between F(u_i) and the sample's empirical CDF (i + 1/2)/m; knot
-//      positions start at sample quantiles, values at i/256; the steps are
-//      captured in a CUDA graph, and the parameters with the lowest loss seen
+//      positions start at sample quantiles, values at i/256; all steps run in
+//      one single-CTA kernel, and the parameters with the lowest loss seen
 //      (the initial ones included) are kept;
 //   3. splitter table: s_b = first key with F(key) >= b/B (fp32, fixed
 //      operation order), made non-decreasing; bucket(key) = #{b in 1..B-1 :
-//      s_b <= key}. The model's proposal floor(F(u) B) is accepted when the
-//      splitters confirm it, else a binary search fixes it (counted);
+//      s_b <= key}. The model's proposal floor(F(u) B) (F through a segment
+//      table and per-segment slopes) is accepted when the splitters confirm
+//      it, else a binary search fixes it (counted);
 //   4. census: bucket sizes, fix-ups, per-chunk counts for the first pass;
 //      too many keys in buckets beyond the on-chip capacity -> plain LSD;
 //   5. stable distribution by bucket: two stable passes over the bucket id's
@@ -53,9 +54,6 @@ constexpr uint64_t kSampleSeed = 0x5EED5EED5EEDull;
 constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
 constexpr int kTrainSteps = 64;
 constexpr float kLearningRate = 0.02f;
-constexpr int kGradCtas = 64;
-constexpr int kGradThreads = 256;
-constexpr int kPartial = 2 * kPwlKnots + 1;  // gX[257] gY[257] loss
 constexpr uint32_t kOnChipCapacity = 65536;  // keys a cluster finishes on chip
 constexpr int kMaxBuckets = 16384;           // the splitter table is held in shared memory
 
@@ -88,38 +86,11 @@ __device__ __forceinline__ float softplus(float t) { return t > 20.f ? t : log1p
 __device__ __forceinline__ float inv_softplus(float v) { return v > 20.f ? v : logf(expm1f(v)); }
 __device__ __forceinline__ float sigmoidf_(float t) { return 1.f / (1.f + expf(-t)); }
 
-// theta[0..255]: knot-position increments; theta[256..511]: value increments.
-// X, Y: cumulative sums of softplus(theta) normalised to end at 1 (one CTA of
-// 256 threads, fixed order, so the result is a function of theta alone).
-__device__ void derive_knots(const float* theta, float* X, float* Y, float* s_tmp) {
-    const int t = threadIdx.x;
-    for (int which = 0; which < 2; ++which) {
-        float* V = which == 0 ? X : Y;
-        s_tmp[t] = softplus(theta[which * kPwlSegments + t]);
-        __syncthreads();
-        if (t == 0) {
-            float run = 0.f;
-            for (int i = 0; i < kPwlSegments; ++i) {
-                const float v = s_tmp[i];
-                s_tmp[i] = run;
-                run += v;
-            }
-            s_tmp[kPwlSegments] = run;
-        }
-        __syncthreads();
-        const float total = s_tmp[kPwlSegments];
-        V[t] = t == 0 ? 0.f : s_tmp[t] / total;
-        if (t == 0) V[kPwlSegments] = 1.f;
-        __syncthreads();
-    }
-}
-
 // Initial parameters from the sorted sample: knot positions at the sample's
-// quantiles j/256, values j/256.
+// quantiles j/256 (increments floored at 1e-3 of the mean), values j/256.
 template <typename K>
 __global__ void __launch_bounds__(kPwlSegments) k_model_init(const K* __restrict__ sorted, uint32_t m, float scale,
-                                                             float* theta, float* X, float* Y, float* adam) {
-    __shared__ float s_tmp[kPwlKnots];
+                                                             float* theta) {
     const int t = threadIdx.x;
     auto q = [&](int j) -> float {
         if (j <= 0) return 0.f;
@@ -130,155 +101,228 @@ __global__ void __launch_bounds__(kPwlSegments) k_model_init(const K* __restrict
     const float dx = fmaxf(q(t + 1) - q(t), 0.f) * (float)kPwlSegments;
     theta[t] = inv_softplus(fmaxf(dx, 1e-3f));
     theta[kPwlSegments + t] = inv_softplus(1.f);
-    adam[t] = adam[kPwlSegments + t] = 0.f;
-    adam[2 * kPwlSegments + t] = adam[3 * kPwlSegments + t] = 0.f;
-    __syncthreads();
-    derive_knots(theta, X, Y, s_tmp);
 }
 
-__global__ void __launch_bounds__(kPwlSegments) k_model_derive(const float* theta, float* X, float* Y) {
-    __shared__ float s_tmp[kPwlKnots];
-    derive_knots(theta, X, Y, s_tmp);
-}
+// One CTA fits the model: all steps in one launch, every reduction in a fixed
+// order except the per-knot gradient sums (shared-memory float atomics).
+constexpr int kFitThreads = 1024;
 
-// Loss and gradient with respect to the knots, partial sums per CTA:
-// L = (1/m) sum_i (F(u_i) - (i + 1/2)/m)^2.
-__global__ void __launch_bounds__(kGradThreads) k_model_grad(const float* __restrict__ u, uint32_t m,
-                                                              const float* __restrict__ X,
-                                                              const float* __restrict__ Y, float* __restrict__ partial) {
-    __shared__ float sX[kPwlKnots], sY[kPwlKnots], gX[kPwlKnots], gY[kPwlKnots];
-    __shared__ float s_loss;
-    const int t = threadIdx.x;
-    for (int i = t; i < kPwlKnots; i += kGradThreads) {
-        sX[i] = X[i];
-        sY[i] = Y[i];
-        gX[i] = 0.f;
-        gY[i] = 0.f;
+__device__ __forceinline__ float warp_incl_scan(float v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float y = __shfl_up_sync(kFullMask, v, o);
+        if (lane >= o) v += y;
     }
-    if (t == 0) s_loss = 0.f;
+    return v;
+}
+
+__device__ __forceinline__ float warp_suffix_scan(float v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float y = __shfl_down_sync(kFullMask, v, o);
+        if (lane + o < 32) v += y;
+    }
+    return v;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFullMask, v, o);
+    return v;
+}
+
+// X, Y from theta: threads 0..255 make X, 256..511 make Y (warps 0-7, 8-15):
+// V_i = (sum_{k<i} softplus(theta_k)) / (sum_k softplus(theta_k)), V_256 = 1.
+__device__ void fit_derive(const float* th, float* X, float* Y, float* wt) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    float v = 0.f, incl = 0.f;
+    if (t < 2 * kPwlSegments) {
+        v = softplus(th[t]);
+        incl = warp_incl_scan(v, lane);
+        if (lane == 31) wt[warp] = incl;
+    }
     __syncthreads();
-    const uint32_t per_cta = (m + gridDim.x - 1) / gridDim.x;
-    const uint32_t c0 = blockIdx.x * per_cta, c1 = min(m, c0 + per_cta);
-    const uint32_t per_thread = (per_cta + kGradThreads - 1) / kGradThreads;
-    const uint32_t p0 = c0 + t * per_thread, p1 = min(c1, p0 + per_thread);  // contiguous points per thread
+    if (t < 2 * kPwlSegments) {
+        const int g = t >> 8, i = t & (kPwlSegments - 1);
+        float before = 0.f, total = 0.f;
+        for (int w = g * 8; w < g * 8 + 8; ++w) {
+            if (w < warp) before += wt[w];
+            total += wt[w];
+        }
+        float excl = __shfl_up_sync(kFullMask, incl, 1);
+        excl = lane == 0 ? before : before + excl;
+        float* V = g ? Y : X;
+        V[i] = i == 0 ? 0.f : fminf(excl / total, 1.f);
+        if (i == 0) V[kPwlSegments] = 1.f;
+    }
+    __syncthreads();
+}
+
+// Loss L = (1/m) sum_i (F(u_i) - (i + 1/2)/m)^2 and its gradient with respect
+// to the knots (gX, gY, zeroed here); u sorted. Each thread takes a contiguous
+// run of points, so its segment index only grows; partial sums are flushed to
+// shared memory when it changes. Returns L (the same value in every thread).
+__device__ float fit_loss_grad(const float* __restrict__ u, uint32_t m, const float* X, const float* Y, float* gX,
+                               float* gY, float* red) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (int j = t; j < kPwlKnots; j += kFitThreads) gX[j] = gY[j] = 0.f;
+    __syncthreads();
+    const uint32_t P = (m + kFitThreads - 1) / kFitThreads;
+    const uint32_t i0 = min(m, (uint32_t)t * P), i1 = min(m, i0 + P);
     const float inv_m = 1.f / (float)m;
     float loss = 0.f;
-    for (uint32_t i = p0; i < p1; ++i) {
-        const float x = u[i];
-        const int j = x < sX[kPwlSegments] ? pwl_segment(sX, x) : kPwlSegments - 1;
-        const float dx = sX[j + 1] - sX[j];
-        const float dy = sY[j + 1] - sY[j];
-        const float w = dx > 0.f ? fminf(fmaxf((x - sX[j]) / dx, 0.f), 1.f) : 0.f;
-        const float f = sY[j] + dy * w;
-        const float e = f - ((float)i + 0.5f) * inv_m;
-        loss += e * e;
-        const float ge = 2.f * e * inv_m;
-        atomicAdd(&gY[j], ge * (1.f - w));
-        atomicAdd(&gY[j + 1], ge * w);
-        if (dx > 0.f && x < sX[j + 1]) {
-            const float k = ge * dy / (dx * dx);
-            atomicAdd(&gX[j], k * (x - sX[j + 1]));
-            atomicAdd(&gX[j + 1], -k * (x - sX[j]));
-        }
-    }
-    atomicAdd(&s_loss, loss * inv_m);
-    __syncthreads();
-    float* out = partial + (size_t)blockIdx.x * kPartial;
-    for (int i = t; i < kPwlKnots; i += kGradThreads) {
-        out[i] = gX[i];
-        out[kPwlKnots + i] = gY[i];
-    }
-    if (t == 0) out[2 * kPwlKnots] = s_loss;
-}
-
-// Reduces the partials (fixed order), maps knot gradients to theta through the
-// normalised softplus sums, and applies one Adam step (lr = 0: gradient only).
-// grad_out (optional): dL/dtheta; loss_out[step]: loss at the current theta.
-// best[0..511], best[512]: the parameters with the lowest loss seen so far.
-// mode kStepPlain: no record; kStepTrain: record (the first step resets it);
-// kStepFinal: keep the current parameters if they beat the record, else
-// restore the record (loss_out[step] then holds the record's loss).
-enum { kStepPlain = 0, kStepTrain = 1, kStepFinal = 2 };
-
-__global__ void __launch_bounds__(kPwlSegments) k_model_step(const float* __restrict__ partial, int parts,
-                                                             float* theta, float* adam, float* X, float* Y,
-                                                             int step, float lr, float* loss_out, float* grad_out,
-                                                             float* best, int mode) {
-    __shared__ float s_g[2][kPwlKnots];
-    __shared__ float s_tmp[kPwlKnots];
-    __shared__ float s_red[2];
-    __shared__ int s_take;  // 1: record the current parameters; 2: restore the record
-    const int t = threadIdx.x;
-    for (int i = t; i < kPwlKnots; i += kPwlSegments) {
-        float gx = 0.f, gy = 0.f;
-        for (int c = 0; c < parts; ++c) {
-            gx += partial[(size_t)c * kPartial + i];
-            gy += partial[(size_t)c * kPartial + kPwlKnots + i];
-        }
-        s_g[0][i] = gx;
-        s_g[1][i] = gy;
-    }
-    if (t == 0) {
-        float l = 0.f;
-        for (int c = 0; c < parts; ++c) l += partial[(size_t)c * kPartial + 2 * kPwlKnots];
-        int take = 0;
-        if (mode == kStepTrain) take = (step == 0 || l < best[2 * kPwlSegments]) ? 1 : 0;
-        if (mode == kStepFinal) take = l < best[2 * kPwlSegments] ? 1 : 2;
-        if (take == 1) best[2 * kPwlSegments] = l;
-        if (take == 2) l = best[2 * kPwlSegments];
-        if (loss_out) loss_out[step] = l;
-        s_take = take;
-    }
-    __syncthreads();
-    if (s_take == 1) {
-        best[t] = theta[t];
-        best[kPwlSegments + t] = theta[kPwlSegments + t];
-    }
-    if (mode == kStepFinal) {
-        if (s_take == 2) {
-            theta[t] = best[t];
-            theta[kPwlSegments + t] = best[kPwlSegments + t];
-        }
-        __syncthreads();
-        derive_knots(theta, X, Y, s_tmp);
-        return;
-    }
-    float dtheta[2];
-    for (int which = 0; which < 2; ++which) {
-        const float* V = which == 0 ? X : Y;
-        const float* g = s_g[which];
-        // A = sum_j g_j V_j ; suffix(i) = sum_{j > i} g_j ; S = sum softplus
-        if (t == 0) {
-            float A = 0.f, S = 0.f;
-            for (int j = 0; j < kPwlKnots; ++j) A += g[j] * V[j];
-            for (int i = 0; i < kPwlSegments; ++i) S += softplus(theta[which * kPwlSegments + i]);
-            s_red[0] = A;
-            s_red[1] = S;
-            float run = 0.f;
-            for (int i = kPwlSegments - 1; i >= 0; --i) {
-                run += g[i + 1];
-                s_tmp[i] = run;
+    if (i0 < i1) {
+        int j = pwl_segment(X, u[i0]);
+        float xj = X[j], xj1 = X[j + 1], yj = Y[j], dy = Y[j + 1] - yj, dx = xj1 - xj;
+        float inv = dx > 0.f ? 1.f / dx : 0.f;
+        float aY0 = 0.f, aY1 = 0.f, aX0 = 0.f, aX1 = 0.f;
+        for (uint32_t base = i0; base < i1; base += 8) {
+            float xs[8];  // loads first, so that eight are in flight
+#pragma unroll
+            for (int r = 0; r < 8; ++r) xs[r] = base + r < i1 ? u[base + r] : 0.f;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+            const uint32_t i = base + r;
+            if (i >= i1) break;
+            const float x = xs[r];
+            if (j < kPwlSegments - 1 && xj1 <= x) {
+                atomicAdd(&gY[j], aY0);
+                atomicAdd(&gY[j + 1], aY1);
+                atomicAdd(&gX[j], aX0);
+                atomicAdd(&gX[j + 1], aX1);
+                aY0 = aY1 = aX0 = aX1 = 0.f;
+                while (j < kPwlSegments - 1 && X[j + 1] <= x) ++j;
+                xj = X[j];
+                xj1 = X[j + 1];
+                yj = Y[j];
+                dy = Y[j + 1] - yj;
+                dx = xj1 - xj;
+                inv = dx > 0.f ? 1.f / dx : 0.f;
+            }
+            const float w = fminf(fmaxf((x - xj) * inv, 0.f), 1.f);
+            const float e = yj + dy * w - ((float)i + 0.5f) * inv_m;
+            loss += e * e;
+            const float ge = 2.f * e * inv_m;
+            aY0 += ge * (1.f - w);
+            aY1 += ge * w;
+            if (dx > 0.f && x < xj1) {
+                const float k = ge * dy * inv * inv;
+                aX0 += k * (x - xj1);
+                aX1 -= k * (x - xj);
+            }
             }
         }
-        __syncthreads();
-        const float th = theta[which * kPwlSegments + t];
-        dtheta[which] = sigmoidf_(th) / s_red[1] * (s_tmp[t] - s_red[0]);
-        __syncthreads();
+        atomicAdd(&gY[j], aY0);
+        atomicAdd(&gY[j + 1], aY1);
+        atomicAdd(&gX[j], aX0);
+        atomicAdd(&gX[j + 1], aX1);
     }
-    for (int which = 0; which < 2; ++which) {
-        const int idx = which * kPwlSegments + t;
-        const float g = dtheta[which];
-        if (grad_out) grad_out[idx] = g;
-        if (lr > 0.f) {
-            const float b1 = 0.9f, b2 = 0.999f;
-            float m1 = adam[idx] = b1 * adam[idx] + (1.f - b1) * g;
-            float m2 = adam[2 * kPwlSegments + idx] = b2 * adam[2 * kPwlSegments + idx] + (1.f - b2) * g * g;
-            const float c1 = 1.f - powf(b1, (float)(step + 1)), c2 = 1.f - powf(b2, (float)(step + 1));
-            theta[idx] -= lr * (m1 / c1) / (sqrtf(m2 / c2) + 1e-8f);
+    loss = warp_sum(loss * inv_m);
+    if (lane == 0) red[warp] = loss;
+    __syncthreads();
+    float L = 0.f;
+    for (int w = 0; w < kFitThreads / 32; ++w) L += red[w];
+    __syncthreads();
+    return L;
+}
+
+// d L / d theta (threads 0..511): with V the knots of one half, g their
+// gradient, S = sum softplus(theta), A = sum_j g_j V_j:
+//   d L / d theta_i = sigmoid(theta_i) / S * (sum_{j > i} g_j - A).
+__device__ float fit_theta_grad(const float* th, const float* X, const float* Y, const float* gX, const float* gY,
+                                float* wt) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    float pa = 0.f, ps = 0.f, suf = 0.f, sp = 0.f;
+    if (t < 2 * kPwlSegments) {
+        const int g = t >> 8, i = t & (kPwlSegments - 1);
+        const float* V = g ? Y : X;
+        const float* G = g ? gY : gX;
+        float prod = G[i] * V[i];
+        if (i == kPwlSegments - 1) prod += G[kPwlSegments] * V[kPwlSegments];
+        sp = softplus(th[t]);
+        pa = warp_sum(prod);
+        ps = warp_sum(sp);
+        suf = warp_suffix_scan(G[i + 1], lane);
+        if (lane == 0) {
+            wt[warp] = pa;
+            wt[16 + warp] = ps;
+            wt[32 + warp] = suf;  // the warp's total (lane 0 holds the whole suffix)
         }
     }
     __syncthreads();
-    derive_knots(theta, X, Y, s_tmp);
+    float d = 0.f;
+    if (t < 2 * kPwlSegments) {
+        const int g = t >> 8;
+        float A = 0.f, S = 0.f, later = 0.f;
+        for (int w = g * 8; w < g * 8 + 8; ++w) {
+            A += wt[w];
+            S += wt[16 + w];
+            if (w > warp) later += wt[32 + w];
+        }
+        d = sigmoidf_(th[t]) / S * ((suf + later) - A);
+    }
+    __syncthreads();
+    return d;
+}
+
+// Fits theta (device, 512; read as the start, written with the result) on the
+// normalised sorted sample u by `steps` Adam steps; keeps the parameters with
+// the lowest loss seen. losses (optional): [step] the loss before each step,
+// [steps] the loss of the returned parameters, [steps + 1] the initial loss.
+// loss0, grad_out (optional): the loss and d L / d theta at the initial theta.
+__global__ void __launch_bounds__(kFitThreads, 1)
+    k_cdf_fit(const float* __restrict__ u, uint32_t m, float* theta, float* X_out, float* Y_out, float* losses,
+              float* loss0, float* grad_out, int steps, float lr) {
+    __shared__ float sX[kPwlKnots], sY[kPwlKnots], gX[kPwlKnots], gY[kPwlKnots];
+    __shared__ float th[2 * kPwlSegments], m1[2 * kPwlSegments], m2[2 * kPwlSegments], best[2 * kPwlSegments];
+    __shared__ float wt[48];
+    __shared__ float red[kFitThreads / 32];
+    const int t = threadIdx.x;
+    if (t < 2 * kPwlSegments) {
+        th[t] = theta[t];
+        best[t] = th[t];
+        m1[t] = m2[t] = 0.f;
+    }
+    __syncthreads();
+    fit_derive(th, sX, sY, wt);
+    float best_loss = INFINITY, first = 0.f;
+    const float b1 = 0.9f, b2 = 0.999f;
+    for (int step = 0;; ++step) {
+        const float L = fit_loss_grad(u, m, sX, sY, gX, gY, red);
+        if (step == 0) first = L;
+        if (losses && step < steps && t == 0) losses[step] = L;
+        if (L < best_loss) {  // L is the same in every thread
+            best_loss = L;
+            if (t < 2 * kPwlSegments) best[t] = th[t];
+        }
+        if (step == steps && !(step == 0 && grad_out)) break;
+        const float d = fit_theta_grad(th, sX, sY, gX, gY, wt);
+        if (step == 0 && grad_out && t < 2 * kPwlSegments) grad_out[t] = d;
+        if (step == steps) break;
+        if (t < 2 * kPwlSegments) {
+            const float a = m1[t] = b1 * m1[t] + (1.f - b1) * d;
+            const float v = m2[t] = b2 * m2[t] + (1.f - b2) * d * d;
+            const float c1 = 1.f - powf(b1, (float)(step + 1)), c2 = 1.f - powf(b2, (float)(step + 1));
+            th[t] -= lr * (a / c1) / (sqrtf(v / c2) + 1e-8f);
+        }
+        __syncthreads();
+        fit_derive(th, sX, sY, wt);
+    }
+    if (t < 2 * kPwlSegments) th[t] = best[t];
+    __syncthreads();
+    fit_derive(th, sX, sY, wt);
+    if (t < 2 * kPwlSegments) theta[t] = th[t];
+    for (int j = t; j < kPwlKnots; j += kFitThreads) {
+        if (X_out) X_out[j] = sX[j];
+        if (Y_out) Y_out[j] = sY[j];
+    }
+    if (t == 0) {
+        if (losses) {
+            losses[steps] = best_loss;
+            losses[steps + 1] = first;
+        }
+        if (loss0) *loss0 = first;
+    }
 }
 
 // ---------------------------------------------------------------- splitters
@@ -319,28 +363,18 @@ __global__ void k_splitters_monotone(K* split, int B) {
 
 // ---------------------------------------------------------------- bucket lookup
 
-// Bucket of a key from the splitter table: #{b in 1..B-1 : s_b <= key}. The
-// model's proposal floor(F(u) B) is tried first.
-template <typename K>
-__device__ __forceinline__ uint32_t bucket_of(K k, const K* s, const float* X, const float* Y, int B, float scale,
-                                              bool* fixed) {
-    const float f = pwl_eval(X, Y, normalise_key(k, scale));
-    int b0 = __float2int_rz(__fmul_rn(f, __int2float_rn(B)));
-    b0 = b0 < 0 ? 0 : (b0 > B - 1 ? B - 1 : b0);
-    if ((b0 == 0 || s[b0] <= k) && (b0 == B - 1 || k < s[b0 + 1])) {
-        *fixed = false;
-        return (uint32_t)b0;
-    }
-    *fixed = true;
-    int lo = 0, hi = B - 1;  // largest b with (b == 0 || s_b <= k)
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s[mid] <= k) lo = mid;
-        else hi = mid - 1;
-    }
-    return (uint32_t)lo;
+constexpr int kSegTable = 1024;  // segment index table over u in [0, 1)
+
+// Shared-memory bytes of a bucket lookup: X, Y, slopes, segment table, splitters.
+__host__ __device__ constexpr size_t bucket_tab_bytes(int B, size_t key_bytes) {
+    return 2 * ((kPwlKnots * 4 + 15) / 16 * 16) + kPwlSegments * 4 + ((kSegTable + 1) + 15) / 16 * 16 +
+           (((size_t)B * key_bytes + 15) / 16 * 16);
 }
 
+// Bucket of a key from the splitter table: #{b in 1..B-1 : s_b <= key}. The
+// model proposes floor(F(u) B) (F evaluated through the segment table and the
+// segment slopes); the splitters accept it, or a bisection over them decides.
+// The result depends on the splitters alone.
 template <typename K>
 struct BucketDigit {
     static constexpr bool kCheap = false;
@@ -354,26 +388,89 @@ struct BucketDigit {
     K* s_split;
     float* s_X;
     float* s_Y;
-    __device__ __forceinline__ size_t table_bytes() const {
-        return 2 * align_up_dev(kPwlKnots * 4, 16) + align_up_dev((size_t)B * sizeof(K), 16);
-    }
+    float* s_slope;
+    uint8_t* s_seg;
+    __device__ __forceinline__ size_t table_bytes() const { return bucket_tab_bytes(B, sizeof(K)); }
     __device__ __forceinline__ void setup(unsigned char* p) {
+        constexpr size_t kv = (kPwlKnots * 4 + 15) / 16 * 16;
         s_X = reinterpret_cast<float*>(p);
-        s_Y = reinterpret_cast<float*>(p + align_up_dev(kPwlKnots * 4, 16));
-        s_split = reinterpret_cast<K*>(p + 2 * align_up_dev(kPwlKnots * 4, 16));
+        s_Y = reinterpret_cast<float*>(p + kv);
+        s_slope = reinterpret_cast<float*>(p + 2 * kv);
+        s_seg = p + 2 * kv + kPwlSegments * 4;
+        s_split = reinterpret_cast<K*>(p + 2 * kv + kPwlSegments * 4 + ((kSegTable + 1) + 15) / 16 * 16);
         for (int i = threadIdx.x; i < kPwlKnots; i += blockDim.x) {
             s_X[i] = g_X[i];
             s_Y[i] = g_Y[i];
         }
         for (int i = threadIdx.x; i < B; i += blockDim.x) s_split[i] = g_split[i];
         __syncthreads();
+        for (int j = threadIdx.x; j < kPwlSegments; j += blockDim.x) {
+            const float dx = s_X[j + 1] - s_X[j];
+            s_slope[j] = dx > 0.f ? (s_Y[j + 1] - s_Y[j]) / dx : 0.f;
+        }
+        for (int q = threadIdx.x; q <= kSegTable; q += blockDim.x)
+            s_seg[q] = (uint8_t)pwl_segment(s_X, (float)q * (1.f / kSegTable));
+        __syncthreads();
+    }
+    __device__ __forceinline__ uint32_t bucket(K k, bool* fixed) const {
+        const float u = normalise_key(k, scale);
+        const int q = min((int)(u * (float)kSegTable), kSegTable - 1);
+        int lo = s_seg[q], hi = s_seg[q + 1];  // lo <= segment(u) <= hi
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_X[mid] <= u) lo = mid;
+            else hi = mid - 1;
+        }
+        const float f = s_Y[lo] + (u - s_X[lo]) * s_slope[lo];
+        int b0 = (int)(f * (float)B);
+        b0 = b0 < 0 ? 0 : (b0 > B - 1 ? B - 1 : b0);
+        if ((b0 == 0 || s_split[b0] <= k) && (b0 == B - 1 || k < s_split[b0 + 1])) {
+            *fixed = false;
+            return (uint32_t)b0;
+        }
+        *fixed = true;
+        int a = 0, c = B - 1;  // largest b with (b == 0 || s_b <= k)
+        while (a < c) {
+            const int mid = (a + c + 1) >> 1;
+            if (s_split[mid] <= k) a = mid;
+            else c = mid - 1;
+        }
+        return (uint32_t)a;
     }
     __device__ __forceinline__ uint32_t bucket(K k) const {
         bool fixed;
-        return bucket_of<K>(k, s_split, s_X, s_Y, B, scale, &fixed);
+        return bucket(k, &fixed);
     }
     __device__ __forceinline__ uint32_t digit(K k) const { return (bucket(k) >> sub_shift) & sub_mask; }
 };
+
+// Loads of a chunk: 16-byte vectors when the base allows, else scalars.
+template <typename K>
+struct KeyVec {
+    static constexpr int kN = 16 / sizeof(K);
+};
+
+template <typename K, typename F>
+__device__ __forceinline__ void for_chunk_keys(const K* __restrict__ keys, uint32_t lo, uint32_t hi, bool vec, F&& f) {
+    constexpr int V = KeyVec<K>::kN;
+    uint32_t i = lo;
+    if (vec) {
+        for (uint32_t b = lo + threadIdx.x * V; b + V <= hi; b += blockDim.x * V) {
+            const uint4 w = *reinterpret_cast<const uint4*>(keys + b);
+            if constexpr (sizeof(K) == 4) {
+                f(b, (K)w.x);
+                f(b + 1, (K)w.y);
+                f(b + 2, (K)w.z);
+                f(b + 3, (K)w.w);
+            } else {
+                f(b, (K)(((uint64_t)w.y << 32) | w.x));
+                f(b + 1, (K)(((uint64_t)w.w << 32) | w.z));
+            }
+        }
+        i = lo + (hi - lo) / V * V;
+    }
+    for (uint32_t b = i + threadIdx.x; b < hi; b += blockDim.x) f(b, keys[b]);
+}
 
 // Census: per-chunk counts of the first pass's digit, every bucket's size
 // (global), the number of proposals the splitters corrected, and the key-range
@@ -386,7 +483,7 @@ __global__ void __launch_bounds__(kCensusThreads) k_bucket_census(const K* __res
                                                                   uint32_t* __restrict__ hist,
                                                                   uint32_t* __restrict__ bucket_count,
                                                                   unsigned long long* fixups, int key_bits,
-                                                                  uint32_t* status) {
+                                                                  uint32_t* status, int vec) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int bins = (int)df.sub_mask + 1;
     uint32_t* s_h = reinterpret_cast<uint32_t*>(smem);             // [bins]
@@ -398,15 +495,14 @@ __global__ void __launch_bounds__(kCensusThreads) k_bucket_census(const K* __res
     const uint32_t lo = blockIdx.x * chunk_keys, hi = min(n, lo + chunk_keys);
     uint32_t fix = 0;
     K kor = 0;
-    for (uint32_t i = lo + threadIdx.x; i < hi; i += kCensusThreads) {
-        const K k = keys[i];
+    for_chunk_keys<K>(keys, lo, hi, vec != 0, [&](uint32_t, K k) {
         kor |= k;
         bool fixed;
-        const uint32_t b = bucket_of<K>(k, df.s_split, df.s_X, df.s_Y, df.B, df.scale, &fixed);
+        const uint32_t b = df.bucket(k, &fixed);
         fix += fixed ? 1u : 0u;
         atomicAdd(&s_h[(b >> df.sub_shift) & df.sub_mask], 1u);
         atomicAdd(&s_b[b], 1u);
-    }
+    });
     __syncthreads();
     for (int i = threadIdx.x; i < bins; i += kCensusThreads) hist[(size_t)blockIdx.x * bins + i] = s_h[i];
     for (int i = threadIdx.x; i < df.B; i += kCensusThreads)
@@ -420,7 +516,7 @@ __global__ void __launch_bounds__(kCensusThreads) k_bucket_census(const K* __res
 template <typename K>
 __global__ void __launch_bounds__(kCensusThreads) k_bucket_hist(const K* __restrict__ keys, uint32_t n,
                                                                 uint32_t chunk_keys, BucketDigit<K> df,
-                                                                uint32_t* __restrict__ hist) {
+                                                                uint32_t* __restrict__ hist, int vec) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int bins = (int)df.sub_mask + 1;
     uint32_t* s_h = reinterpret_cast<uint32_t*>(smem);
@@ -428,7 +524,7 @@ __global__ void __launch_bounds__(kCensusThreads) k_bucket_hist(const K* __restr
     for (int i = threadIdx.x; i < bins; i += kCensusThreads) s_h[i] = 0;
     df.setup(tab);
     const uint32_t lo = blockIdx.x * chunk_keys, hi = min(n, lo + chunk_keys);
-    for (uint32_t i = lo + threadIdx.x; i < hi; i += kCensusThreads) atomicAdd(&s_h[df.digit(keys[i])], 1u);
+    for_chunk_keys<K>(keys, lo, hi, vec != 0, [&](uint32_t, K k) { atomicAdd(&s_h[df.digit(k)], 1u); });
     __syncthreads();
     for (int i = threadIdx.x; i < bins; i += kCensusThreads) hist[(size_t)blockIdx.x * bins + i] = s_h[i];
 }
@@ -444,65 +540,12 @@ __global__ void k_bucket_ids(const K* __restrict__ keys, uint32_t n, BucketDigit
 
 // ---------------------------------------------------------------- host side
 
-struct ModelBufs {
-    float* u;        // normalised sorted sample [m]
-    float* theta;    // [512]
-    float* adam;     // [1024]
-    float* best;     // [513]: best parameters so far and their loss
-    float* X;        // [257]
-    float* Y;        // [257]
-    float* partial;  // [kGradCtas][kPartial]
-    float* losses;   // [kTrainSteps + 1]
-};
-
-isort_status launch_grad_step(const ModelBufs& mb, uint32_t m, int step, float lr, float* grad_out, int mode,
-                              cudaStream_t s) {
-    {
-        LaunchScope ls("cdf_grad", s);
-        k_model_grad<<<kGradCtas, kGradThreads, 0, s>>>(mb.u, m, mb.X, mb.Y, mb.partial);
-        ISORT_TRY_CUDA(cudaGetLastError());
-    }
-    LaunchScope ls("cdf_step", s);
-    k_model_step<<<1, kPwlSegments, 0, s>>>(mb.partial, kGradCtas, mb.theta, mb.adam, mb.X, mb.Y, step, lr,
-                                           mb.losses, grad_out, mb.best, mode);
+// Fits the model on u (device, m normalised sorted sample values); see k_cdf_fit.
+isort_status launch_fit(const float* u, uint32_t m, float* theta, float* X, float* Y, float* losses, float* loss0,
+                        float* grad, int steps, cudaStream_t s) {
+    LaunchScope ls("cdf_fit", s);
+    k_cdf_fit<<<1, kFitThreads, 0, s>>>(u, m, theta, X, Y, losses, loss0, grad, steps, kLearningRate);
     return from_cuda(cudaGetLastError());
-}
-
-// kTrainSteps Adam steps, captured once per call into a CUDA graph.
-isort_status train_model(const ModelBufs& mb, uint32_t m, int steps, cudaStream_t s) {
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    cudaStreamIsCapturing(s, &cap);
-    if (cap == cudaStreamCaptureStatusActive) {
-        for (int i = 0; i < steps; ++i) {
-            isort_status st = launch_grad_step(mb, m, i, kLearningRate, nullptr, kStepTrain, s);
-            if (st != ISORT_OK) return st;
-        }
-    } else {
-        cudaStream_t cs = nullptr;
-        ISORT_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-        cudaGraph_t g = nullptr;
-        cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        isort_status st = ISORT_OK;
-        if (ce == cudaSuccess) {
-            CaptureScope scope;
-            for (int i = 0; i < steps && st == ISORT_OK; ++i)
-                st = launch_grad_step(mb, m, i, kLearningRate, nullptr, kStepTrain, cs);
-            ce = cudaStreamEndCapture(cs, &g);
-        }
-        cudaGraphExec_t ex = nullptr;
-        if (ce == cudaSuccess && st == ISORT_OK) ce = cudaGraphInstantiate(&ex, g, 0);
-        if (ce == cudaSuccess && st == ISORT_OK) {
-            LaunchScope ls("cdf_train_graph", s, false);
-            ce = cudaGraphLaunch(ex, s);
-        }
-        if (ex) cudaGraphExecDestroy(ex);
-        if (g) cudaGraphDestroy(g);
-        cudaStreamDestroy(cs);
-        if (st != ISORT_OK) return st;
-        if (ce != cudaSuccess) return from_cuda(ce);
-    }
-    // the loss of the final parameters; the best ones seen are kept
-    return launch_grad_step(mb, m, steps, 0.f, nullptr, kStepFinal, s);
 }
 
 int ceil_log2(uint32_t v) {
@@ -525,7 +568,7 @@ isort_status launch_bucket_sweep(const SweepArgs& a, const BucketDigit<K>& df, u
                                  cudaStream_t s) {
     using Cfg = SweepCfg<K, true, 512, 8>;
     using CfgK = SweepCfg<K, false, 512, 8>;
-    const size_t tb = 2 * align_up(kPwlKnots * 4, 16) + align_up((size_t)df.B * sizeof(K), 16);
+    const size_t tb = bucket_tab_bytes(df.B, sizeof(K));
     LaunchScope ls("bucket_sweep", s);
     if (vals) {
         const size_t smem = Cfg::smem_bytes(a.bins, false, tb);
@@ -556,7 +599,7 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
     // launch geometry of the distribution passes
     using Cfg = SweepCfg<K, true, 512, 8>;
     const uint32_t tile = 512 * 8;
-    const size_t tb = 2 * align_up(kPwlKnots * 4, 16) + align_up((size_t)B * sizeof(K), 16);
+    const size_t tb = bucket_tab_bytes(B, sizeof(K));
     const size_t sweep_smem = Cfg::smem_bytes(bins, false, tb);
     const size_t census_smem = align_up((size_t)bins * 4 + align_up((size_t)B, 4) * 4, 16) + tb;
     if (sweep_smem > max_smem_optin() || census_smem > max_smem_optin()) return ISORT_ERR_UNSUPPORTED;
@@ -581,10 +624,9 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
     };
     const size_t o_status = take(64), o_fix = take(64);
     const size_t o_sample = take((size_t)m * sizeof(K)), o_u = take((size_t)m * 4);
-    const size_t o_theta = take(2 * kPwlSegments * 4), o_adam = take(4 * kPwlSegments * 4);
-    const size_t o_best = take((2 * kPwlSegments + 1) * 4);
+    const size_t o_theta = take(2 * kPwlSegments * 4);
     const size_t o_X = take(kPwlKnots * 4), o_Y = take(kPwlKnots * 4);
-    const size_t o_part = take((size_t)kGradCtas * kPartial * 4), o_loss = take((kTrainSteps + 2) * 4);
+    const size_t o_loss = take((kTrainSteps + 2) * 4);
     const size_t o_split = take((size_t)B * sizeof(K)), o_bcount = take((size_t)B * 4);
     const size_t o_hist = take((size_t)chunks * bins * 4), o_coff = take((size_t)chunks * bins * 4);
     const size_t o_segoff = take((size_t)(B + 1) * 8), o_seglo = take((size_t)B * 4), o_segbits = take((size_t)B);
@@ -599,15 +641,11 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
     uint32_t* status = reinterpret_cast<uint32_t*>(ws + o_status);
     unsigned long long* fixups = reinterpret_cast<unsigned long long*>(ws + o_fix);
     K* sample = reinterpret_cast<K*>(ws + o_sample);
-    ModelBufs mb;
-    mb.u = reinterpret_cast<float*>(ws + o_u);
-    mb.theta = reinterpret_cast<float*>(ws + o_theta);
-    mb.adam = reinterpret_cast<float*>(ws + o_adam);
-    mb.best = reinterpret_cast<float*>(ws + o_best);
-    mb.X = reinterpret_cast<float*>(ws + o_X);
-    mb.Y = reinterpret_cast<float*>(ws + o_Y);
-    mb.partial = reinterpret_cast<float*>(ws + o_part);
-    mb.losses = reinterpret_cast<float*>(ws + o_loss);
+    float* u = reinterpret_cast<float*>(ws + o_u);
+    float* theta = reinterpret_cast<float*>(ws + o_theta);
+    float* X = reinterpret_cast<float*>(ws + o_X);
+    float* Y = reinterpret_cast<float*>(ws + o_Y);
+    float* losses = reinterpret_cast<float*>(ws + o_loss);
     K* split = reinterpret_cast<K*>(ws + o_split);
     uint32_t* bcount = reinterpret_cast<uint32_t*>(ws + o_bcount);
     uint32_t* hist = reinterpret_cast<uint32_t*>(ws + o_hist);
@@ -636,42 +674,40 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
     // 2. train the model
     {
         LaunchScope ls("cdf_init", s);
-        k_normalise<K><<<(m + 255) / 256, 256, 0, s>>>(sample, m, scale, mb.u);
-        k_model_init<K><<<1, kPwlSegments, 0, s>>>(sample, m, scale, mb.theta, mb.X, mb.Y, mb.adam);
+        k_normalise<K><<<(m + 255) / 256, 256, 0, s>>>(sample, m, scale, u);
+        k_model_init<K><<<1, kPwlSegments, 0, s>>>(sample, m, scale, theta);
         ce = cudaGetLastError();
         if (ce != cudaSuccess) return fail(from_cuda(ce));
     }
-    // the loss before training
-    st = launch_grad_step(mb, m, kTrainSteps + 1, 0.f, nullptr, kStepPlain, s);
-    if (st != ISORT_OK) return fail(st);
-    st = train_model(mb, m, kTrainSteps, s);
+    st = launch_fit(u, m, theta, X, Y, losses, nullptr, nullptr, kTrainSteps, s);
     if (st != ISORT_OK) return fail(st);
 
     // 3. splitters
     {
         LaunchScope ls("splitters", s);
-        k_splitters<K><<<(B + 255) / 256, 256, 0, s>>>(mb.X, mb.Y, B, key_bits, scale, split);
+        k_splitters<K><<<(B + 255) / 256, 256, 0, s>>>(X, Y, B, key_bits, scale, split);
         k_splitters_monotone<K><<<1, 32, 0, s>>>(split, B);
         ce = cudaGetLastError();
         if (ce != cudaSuccess) return fail(from_cuda(ce));
     }
     BucketDigit<K> df;
     df.g_split = split;
-    df.g_X = mb.X;
-    df.g_Y = mb.Y;
+    df.g_X = X;
+    df.g_Y = Y;
     df.B = B;
     df.scale = scale;
     df.sub_shift = 0;
     df.sub_mask = (uint32_t)bins - 1u;
 
     // 4. census
+    const int vec = ((uintptr_t)keys % 16) == 0 ? 1 : 0;
     {
         const size_t smem = census_smem;
         ce = cudaFuncSetAttribute(k_bucket_census<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (ce != cudaSuccess) return fail(from_cuda(ce));
         LaunchScope ls("bucket_census", s);
         k_bucket_census<K><<<chunks, kCensusThreads, smem, s>>>(keys, (uint32_t)n, chunk_tiles * tile, df, hist, bcount,
-                                                              fixups, key_bits, status);
+                                                              fixups, key_bits, status, vec);
         ce = cudaGetLastError();
         if (ce != cudaSuccess) return fail(from_cuda(ce));
     }
@@ -683,7 +719,7 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
     ce = cudaMemcpyAsync(h_count.data(), bcount, (size_t)B * 4, cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(&h_status, status, 4, cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_split.data(), split, (size_t)B * sizeof(K), cudaMemcpyDeviceToHost, s);
-    if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_loss.data(), mb.losses, (kTrainSteps + 2) * 4, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_loss.data(), losses, (kTrainSteps + 2) * 4, cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(&h_fix, fixups, 8, cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess) return fail(from_cuda(ce));
@@ -727,7 +763,9 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
             ce = cudaFuncSetAttribute(k_bucket_hist<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (ce != cudaSuccess) return fail(from_cuda(ce));
             LaunchScope ls("bucket_hist", s);
-            k_bucket_hist<K><<<chunks, kCensusThreads, smem, s>>>(src_k, (uint32_t)n, chunk_tiles * tile, df, hist);
+            const int pvec = ((uintptr_t)src_k % 16) == 0 ? 1 : 0;
+            k_bucket_hist<K><<<chunks, kCensusThreads, smem, s>>>(src_k, (uint32_t)n, chunk_tiles * tile, df, hist,
+                                                                pvec);
             ce = cudaGetLastError();
             if (ce != cudaSuccess) return fail(from_cuda(ce));
         }
@@ -820,7 +858,12 @@ isort_status isort_learned(uint32_t* keys, uint32_t* vals, size_t n, int key_bit
     std::memset(st, 0, sizeof(*st));
     if (key_bits == 0) key_bits = 32;
     if (key_bits < 1 || key_bits > 32) return ISORT_ERR_INVALID_ARG;
-    if (nbuckets == 0) nbuckets = 4096;
+    if (nbuckets == 0) {
+        // 4096 buckets, doubled (up to the table limit) while the mean bucket
+        // would exceed a quarter of the on-chip capacity
+        nbuckets = 4096;
+        while (nbuckets < kMaxBuckets && (uint64_t)nbuckets * (kOnChipCapacity / 4) < n) nbuckets <<= 1;
+    }
     if (nbuckets < 2 || nbuckets > kMaxBuckets) return ISORT_ERR_INVALID_ARG;
     if (model != 0 && model != 1) return ISORT_ERR_INVALID_ARG;
     if (model == 1) return ISORT_ERR_UNSUPPORTED;
@@ -873,15 +916,15 @@ isort_status isort_bucket_ids(const void* keys, int key_width, size_t n, int key
     LaunchScope ls("bucket_ids", s);
     if (key_width == 32) {
         BucketDigit<uint32_t> df{static_cast<const uint32_t*>(splitters), X, Y, nbuckets, scale, 0, 0xffffu,
-                                 nullptr, nullptr, nullptr};
-        const size_t smem = 2 * align_up(kPwlKnots * 4, 16) + align_up((size_t)nbuckets * 4, 16);
+                                 nullptr, nullptr, nullptr, nullptr, nullptr};
+        const size_t smem = bucket_tab_bytes(nbuckets, 4);
         ISORT_TRY_CUDA(cudaFuncSetAttribute(k_bucket_ids<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)smem));
         k_bucket_ids<uint32_t><<<grid, 256, smem, s>>>(static_cast<const uint32_t*>(keys), (uint32_t)n, df, ids);
     } else {
         BucketDigit<uint64_t> df{static_cast<const uint64_t*>(splitters), X, Y, nbuckets, scale, 0, 0xffffu,
-                                 nullptr, nullptr, nullptr};
-        const size_t smem = 2 * align_up(kPwlKnots * 4, 16) + align_up((size_t)nbuckets * 8, 16);
+                                 nullptr, nullptr, nullptr, nullptr, nullptr};
+        const size_t smem = bucket_tab_bytes(nbuckets, 8);
         ISORT_TRY_CUDA(cudaFuncSetAttribute(k_bucket_ids<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)smem));
         k_bucket_ids<uint64_t><<<grid, 256, smem, s>>>(static_cast<const uint64_t*>(keys), (uint32_t)n, df, ids);
@@ -895,34 +938,12 @@ isort_status isort_cdf_loss_grad(const float* u, uint32_t m, const float* theta,
                                  void* stream) {
     if (!u || !theta || !grad || !loss || m == 0) return ISORT_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    float* buf = nullptr;
-    // theta copy, adam, X, Y, partials
-    const size_t floats = 2 * kPwlSegments + 4 * kPwlSegments + 2 * kPwlKnots + (size_t)kGradCtas * kPartial;
-    isort_status st = scratch_alloc((void**)&buf, floats * 4, s);
+    float* th = nullptr;  // the fit writes its parameters back: work on a copy
+    isort_status st = scratch_alloc((void**)&th, 2 * kPwlSegments * 4, s);
     if (st != ISORT_OK) return st;
-    ModelBufs mb;
-    mb.u = const_cast<float*>(u);
-    mb.theta = buf;
-    mb.adam = buf + 2 * kPwlSegments;
-    mb.X = mb.adam + 4 * kPwlSegments;
-    mb.Y = mb.X + kPwlKnots;
-    mb.partial = mb.Y + kPwlKnots;
-    mb.best = nullptr;
-    mb.losses = loss;  // loss_out[0]
-    cudaError_t ce = cudaMemcpyAsync(mb.theta, theta, 2 * kPwlSegments * 4, cudaMemcpyDeviceToDevice, s);
-    if (ce == cudaSuccess) ce = cudaMemsetAsync(mb.adam, 0, 4 * kPwlSegments * 4, s);
-    if (ce != cudaSuccess) {
-        scratch_free(buf, s);
-        return from_cuda(ce);
-    }
-    {
-        LaunchScope ls("cdf_derive", s);
-        k_model_derive<<<1, kPwlSegments, 0, s>>>(mb.theta, mb.X, mb.Y);
-        ce = cudaGetLastError();
-    }
-    if (ce == cudaSuccess) st = launch_grad_step(mb, m, 0, 0.f, grad, kStepPlain, s);
-    else st = from_cuda(ce);
-    scratch_free(buf, s);
+    cudaError_t ce = cudaMemcpyAsync(th, theta, 2 * kPwlSegments * 4, cudaMemcpyDeviceToDevice, s);
+    st = ce == cudaSuccess ? launch_fit(u, m, th, nullptr, nullptr, nullptr, loss, grad, 0, s) : from_cuda(ce);
+    scratch_free(th, s);
     if (st == ISORT_OK && sync_mode()) st = from_cuda(cudaStreamSynchronize(s));
     return st;
 }
@@ -933,29 +954,18 @@ isort_status isort_cdf_train(const uint32_t* sorted_sample, uint32_t m, int key_
     if (key_bits == 0) key_bits = 32;
     if (key_bits < 1 || key_bits > 32) return ISORT_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    float* buf = nullptr;
-    const size_t floats = (size_t)m + 4 * kPwlSegments + (size_t)kGradCtas * kPartial + 2 * kPwlSegments + 1;
-    isort_status st = scratch_alloc((void**)&buf, floats * 4, s);
+    float* u = nullptr;
+    isort_status st = scratch_alloc((void**)&u, (size_t)m * 4, s);
     if (st != ISORT_OK) return st;
-    ModelBufs mb;
-    mb.u = buf;
-    mb.adam = buf + m;
-    mb.partial = mb.adam + 4 * kPwlSegments;
-    mb.best = mb.partial + (size_t)kGradCtas * kPartial;
-    mb.theta = theta;
-    mb.X = X;
-    mb.Y = Y;
-    mb.losses = losses;  // [kTrainSteps + 2]: per step, then the initial loss last
     const float scale = std::ldexp(1.0f, -key_bits);
     {
         LaunchScope ls("cdf_init", s);
-        k_normalise<uint32_t><<<(m + 255) / 256, 256, 0, s>>>(sorted_sample, m, scale, mb.u);
-        k_model_init<uint32_t><<<1, kPwlSegments, 0, s>>>(sorted_sample, m, scale, mb.theta, mb.X, mb.Y, mb.adam);
+        k_normalise<uint32_t><<<(m + 255) / 256, 256, 0, s>>>(sorted_sample, m, scale, u);
+        k_model_init<uint32_t><<<1, kPwlSegments, 0, s>>>(sorted_sample, m, scale, theta);
         st = from_cuda(cudaGetLastError());
     }
-    if (st == ISORT_OK) st = launch_grad_step(mb, m, kTrainSteps + 1, 0.f, nullptr, kStepPlain, s);
-    if (st == ISORT_OK) st = train_model(mb, m, kTrainSteps, s);
-    scratch_free(buf, s);
+    if (st == ISORT_OK) st = launch_fit(u, m, theta, X, Y, losses, nullptr, nullptr, kTrainSteps, s);
+    scratch_free(u, s);
     if (st == ISORT_OK && sync_mode()) st = from_cuda(cudaStreamSynchronize(s));
     return st;
 }

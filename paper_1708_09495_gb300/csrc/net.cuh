@@ -26,17 +26,24 @@ constexpr uint64_t kPadHi = 0xFFFFFFFFull << 32;
 __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 __device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a < b ? b : a; }
 
-template <int B>
-__device__ __forceinline__ void cswap(uint64_t (&x)[B], int i, int l, bool asc) {
-    const uint64_t a = x[i], b = x[l];
-    const bool sw = asc ? (a > b) : (a < b);
-    x[i] = sw ? b : a;
-    x[l] = sw ? a : b;
+// The networks below work on 64-bit items (key << 32 | index) or on packed
+// 32-bit items; T is the item type.
+template <typename T>
+__device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
+template <typename T>
+__device__ __forceinline__ T tmax(T a, T b) { return a < b ? b : a; }
+
+template <int B, typename T = uint64_t>
+__device__ __forceinline__ void cswap(T (&x)[B], int i, int l, bool asc) {
+    const T a = x[i], b = x[l];
+    const T lo = tmin(a, b), hi = tmax(a, b);
+    x[i] = asc ? lo : hi;
+    x[l] = asc ? hi : lo;
 }
 
 // Local sort of a block (a register bitonic sorting network, ascending).
-template <int B>
-__device__ __forceinline__ void local_sort(uint64_t (&x)[B]) {
+template <int B, typename T = uint64_t>
+__device__ __forceinline__ void local_sort(T (&x)[B]) {
 #pragma unroll
     for (int k = 2; k <= B; k <<= 1)
 #pragma unroll
@@ -44,19 +51,19 @@ __device__ __forceinline__ void local_sort(uint64_t (&x)[B]) {
 #pragma unroll
             for (int i = 0; i < B; ++i) {
                 const int l = i ^ j;
-                if (l > i) cswap<B>(x, i, l, (i & k) == 0);
+                if (l > i) cswap<B, T>(x, i, l, (i & k) == 0);
             }
 }
 
 // Sorts a bitonic block ascending.
-template <int B>
-__device__ __forceinline__ void bitonic_merge(uint64_t (&x)[B]) {
+template <int B, typename T = uint64_t>
+__device__ __forceinline__ void bitonic_merge(T (&x)[B]) {
 #pragma unroll
     for (int j = B >> 1; j > 0; j >>= 1)
 #pragma unroll
         for (int i = 0; i < B; ++i) {
             const int l = i ^ j;
-            if (l > i) cswap<B>(x, i, l, true);
+            if (l > i) cswap<B, T>(x, i, l, true);
         }
 }
 
@@ -97,19 +104,19 @@ __device__ __forceinline__ void store_block(const uint64_t (&x)[B], uint32_t* ke
 
 // Half-cleaner against the partner lane (t ^ j) of the same warp. Slots i and
 // B-1-i are exchanged together so that only original values are sent.
-template <int B>
-__device__ __forceinline__ void merge_split_shfl(uint64_t (&x)[B], int j, bool keep_small) {
+template <int B, typename T = uint64_t>
+__device__ __forceinline__ void merge_split_shfl(T (&x)[B], int j, bool keep_small) {
     if constexpr (B == 1) {
-        const uint64_t y = __shfl_xor_sync(kFullMask, x[0], j);
-        x[0] = keep_small ? umin64(x[0], y) : umax64(x[0], y);
+        const T y = __shfl_xor_sync(kFullMask, x[0], j);
+        x[0] = keep_small ? tmin(x[0], y) : tmax(x[0], y);
     } else {
 #pragma unroll
         for (int i = 0; i < B / 2; ++i) {
-            const uint64_t a = x[i], b = x[B - 1 - i];
-            const uint64_t ya = __shfl_xor_sync(kFullMask, b, j);  // partner's item B-1-i
-            const uint64_t yb = __shfl_xor_sync(kFullMask, a, j);  // partner's item i
-            x[i] = keep_small ? umin64(a, ya) : umax64(a, ya);
-            x[B - 1 - i] = keep_small ? umin64(b, yb) : umax64(b, yb);
+            const T a = x[i], b = x[B - 1 - i];
+            const T ya = __shfl_xor_sync(kFullMask, b, j);  // partner's item B-1-i
+            const T yb = __shfl_xor_sync(kFullMask, a, j);  // partner's item i
+            x[i] = keep_small ? tmin(a, ya) : tmax(a, ya);
+            x[B - 1 - i] = keep_small ? tmin(b, yb) : tmax(b, yb);
         }
     }
 }

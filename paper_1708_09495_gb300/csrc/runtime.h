@@ -63,3 +63,9 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
         cudaError_t e_ = (expr);                             \
         if (e_ != cudaSuccess) return ::isort::from_cuda(e_); \
     } while (0)
+
+#define ISORT_TRY(expr)                       \
+    do {                                      \
+        isort_status s_ = (expr);             \
+        if (s_ != ISORT_OK) return s_;        \
+    } while (0)

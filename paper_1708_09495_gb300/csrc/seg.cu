@@ -5,19 +5,24 @@
 // Observations 5 and 6):
 //   len <= T_oet           OET in one warp, one key per lane (Section 2)
 //   len <= T_btn_warp      BTN in one warp, 8 keys per lane (Section 2, eq. Tb)
-//   len <= T_btn_cta       BTN over a 512-thread CTA, 8 keys per thread
-//   len <= 8 * 8192        count-sort rounds (8-bit digits, Section 3) entirely
-//                          on chip: a thread-block cluster of C = 1, 2, 4 or 8
-//                          CTAs holds the segment, 8192 keys per CTA; each round
-//                          ranks keys per CTA, exchanges the C digit histograms
-//                          through distributed shared memory, and scatters
-//                          every key straight into the shared memory of the CTA
-//                          that owns its new position. HBM sees one read and
-//                          one write per key.
+//   len <= T_btn_cta       BTN over a CTA of p = next_pow2(len / 8) threads,
+//                          8 keys per thread (four classes: p = 64 .. 512)
+//   len <= 8192            count-sort rounds (8-bit digits, Section 3) entirely
+//                          on chip in one CTA (the cluster kernel with C = 1).
+//   len <= 8 * 8192        a thread-block cluster of C = 2, 4 or 8 CTAs (8192
+//                          keys each) runs one count-sort round on the top 8
+//                          bits of the segment's key range, the C digit
+//                          histograms exchanged through distributed shared
+//                          memory, and writes the result in place; its warps
+//                          then finish the 256 digit groups (L2-resident) with
+//                          BTN in registers, splitting a group above 512 keys
+//                          again on its next 8 bits (MSD order). Segments over
+//                          4 * 8192 keys with payloads split on 9 bits.
 //   longer                 the global LSD path, one segment at a time (host
 //                          driven; only in the synchronous status mode).
 // Routing happens on the device: a classification kernel builds one work
-// list per class, and persistent kernels pull segments from their list.
+// list per class, and persistent kernels walk their list with a static stride
+// (warp, CTA or cluster index; no shared work counter).
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -46,7 +51,20 @@ constexpr int kSegBins = 256;
 constexpr int kSegWarps = kSegThreads / 32;
 static_assert(kSegChunk == 1 << kSegChunkLog, "chunk is a power of two");
 
-enum : int { kClsOet = 0, kClsBtnWarp, kClsBtnCta, kClsC1, kClsC2, kClsC4, kClsC8, kClsBig, kNumCls };
+enum : int {
+    kClsOet = 0,
+    kClsBtnWarp,
+    kClsCta64,  // BTN over a CTA of p threads, p = next power of two >= len / 8
+    kClsCta128,
+    kClsCta256,
+    kClsCta512,
+    kClsC1,
+    kClsC2,
+    kClsC4,
+    kClsC8,
+    kClsBig,
+    kNumCls
+};
 
 struct SegThresholds {
     uint32_t oet;       // <= : OET in a warp (at most 32)
@@ -74,7 +92,7 @@ __global__ void k_seg_classify(const uint64_t* off, uint32_t nseg, SegThresholds
         int c;
         if (L <= th.oet) c = kClsOet;
         else if (L <= th.btn_warp) c = kClsBtnWarp;
-        else if (L <= th.btn_cta) c = kClsBtnCta;
+        else if (L <= th.btn_cta) c = L <= 512 ? kClsCta64 : L <= 1024 ? kClsCta128 : L <= 2048 ? kClsCta256 : kClsCta512;
         else if (L <= (uint64_t)kSegChunk) c = kClsC1;
         else if (L <= 2ull * kSegChunk) c = kClsC2;
         else if (L <= 4ull * kSegChunk) c = kClsC4;
@@ -90,13 +108,9 @@ __global__ void k_seg_classify(const uint64_t* off, uint32_t nseg, SegThresholds
 template <bool OET>
 __global__ void __launch_bounds__(256) k_seg_warp(uint32_t* keys, uint32_t* vals, const uint64_t* off,
                                                   const uint32_t* list, SegCtl* ctl, int cls, uint32_t range_mask) {
-    const int lane = threadIdx.x & 31;
     const uint32_t cnt = ctl->counts[cls];
-    while (true) {
-        uint32_t q = 0;
-        if (lane == 0) q = atomicAdd(&ctl->work[cls], 1u);
-        q = __shfl_sync(kFullMask, q, 0);
-        if (q >= cnt) break;
+    const uint32_t nwarps = gridDim.x * (blockDim.x / 32);
+    for (uint32_t q = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); q < cnt; q += nwarps) {
         const uint32_t s = list[q];
         const uint64_t lo = off[s];
         const uint32_t L = (uint32_t)(off[s + 1] - lo);
@@ -113,24 +127,19 @@ __global__ void __launch_bounds__(256) k_seg_warp(uint32_t* keys, uint32_t* vals
     }
 }
 
-// One CTA per segment: BTN with p = next_pow2(len / 8) <= 512 blocks of 8.
-__global__ void __launch_bounds__(512) k_seg_btn_cta(uint32_t* keys, uint32_t* vals, const uint64_t* off,
-                                                     const uint32_t* list, SegCtl* ctl, int cls, uint32_t range_mask) {
-    extern __shared__ __align__(16) uint64_t s_x[];
-    __shared__ uint32_t s_q;
+// One CTA of P threads per segment: BTN with p = P blocks of 8 (the class
+// holds the segments with next_pow2(len / 8) = P).
+template <int P>
+__global__ void __launch_bounds__(P) k_seg_btn_cta(uint32_t* keys, uint32_t* vals, const uint64_t* off,
+                                                   const uint32_t* list, SegCtl* ctl, int cls, uint32_t range_mask) {
+    __shared__ uint64_t s_x[8 * P];
     const uint32_t cnt = ctl->counts[cls];
-    while (true) {
-        if (threadIdx.x == 0) s_q = atomicAdd(&ctl->work[cls], 1u);
-        __syncthreads();
-        const uint32_t q = s_q;
-        __syncthreads();
-        if (q >= cnt) break;
+    for (uint32_t q = blockIdx.x; q < cnt; q += gridDim.x) {
         const uint32_t s = list[q];
         const uint64_t lo = off[s];
         const uint32_t L = (uint32_t)(off[s + 1] - lo);
-        int p = 1;
-        while ((uint32_t)(p * 8) < L) p <<= 1;
-        net::btn_block<8>(keys + lo, vals ? vals + lo : nullptr, L, p, s_x, nullptr, range_mask, &ctl->status);
+        net::btn_block<8>(keys + lo, vals ? vals + lo : nullptr, L, P, s_x, nullptr, range_mask, &ctl->status);
+        __syncthreads();  // s_x is reused by the next segment
     }
 }
 
@@ -148,7 +157,7 @@ struct ClusterArgs {
 
 constexpr size_t cluster_smem_bytes(bool vals) {
     return (size_t)kSegChunk * 4 * (vals ? 2 : 1) + (size_t)kSegWarps * kSegBins * 2 + (size_t)kSegBins * 4 * 3 +
-           64 * 4;
+           64 * 4 + (size_t)kSegWarps * kSegBins * 4;
 }
 
 // Count-sort rounds of one segment on a cluster of C CTAs (see file comment).
@@ -161,10 +170,11 @@ __global__ void __launch_bounds__(kSegThreads, 2) k_seg_cluster(ClusterArgs a) {
     uint32_t* s_cta = reinterpret_cast<uint32_t*>(s_cnt + kSegWarps * kSegBins);  // this CTA's digit totals
     uint32_t* s_pre = s_cta + kSegBins;                                            // earlier CTAs' counts
     uint32_t* s_base = s_pre + kSegBins;                                           // digit start + s_pre
-    uint32_t* s_misc = s_base + kSegBins;  // [0] work item, [1] range flag, [8..] warp sums
+    uint32_t* s_misc = s_base + kSegBins;  // [1] range flag, [8..] warp sums
+    uint32_t* s_match = s_misc + 64;       // per warp and digit: lanes holding the digit
     // (the launch always provides cluster_smem_bytes; every CTA of a cluster
     // sees the same size, so a failed check leaves the cluster together)
-    if ((size_t)(reinterpret_cast<unsigned char*>(s_misc + 64) - smem) > dynamic_smem_size()) {
+    if ((size_t)(reinterpret_cast<unsigned char*>(s_match + kSegWarps * kSegBins) - smem) > dynamic_smem_size()) {
         if (threadIdx.x == 0) set_status(&a.ctl->status, kStatBounds);
         return;
     }
@@ -174,13 +184,16 @@ __global__ void __launch_bounds__(kSegThreads, 2) k_seg_cluster(ClusterArgs a) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t cnt = a.ctl->counts[a.cls];
 
-    for (int i = tid; i < kSegWarps * kSegBins; i += kSegThreads) s_cnt[i] = 0;
+    for (int i = tid; i < kSegWarps * kSegBins; i += kSegThreads) {
+        s_cnt[i] = 0;
+        s_match[i] = 0;
+    }
+    __syncthreads();
 
-    while (true) {
-        if (r == 0 && tid == 0) s_misc[0] = atomicAdd(&a.ctl->work[a.cls], 1u);
-        cluster.sync();
-        const uint32_t q = C == 1 ? s_misc[0] : *cluster.map_shared_rank(&s_misc[0], 0);
-        if (q >= cnt) break;
+    // static assignment: cluster c takes list entries c, c + clusters, ...
+    // (every CTA of a cluster walks the same entries)
+    const uint32_t nclusters = gridDim.x / C;
+    for (uint32_t q = blockIdx.x / C; q < cnt; q += nclusters) {
         const uint32_t s = a.list[q];
         const uint64_t lo = a.off[s];
         const uint32_t L = (uint32_t)(a.off[s + 1] - lo);
@@ -209,24 +222,27 @@ __global__ void __launch_bounds__(kSegThreads, 2) k_seg_cluster(ClusterArgs a) {
         bool bad = false;
         for (int d = 0; d < rounds; ++d) {
             const int shift = d * 8;
-            // rank each key among equal digits of its warp, in input order
+            // rank each key among equal digits of its warp, in input order:
+            // the lanes holding a digit OR their bit into the warp's word for
+            // it, read the word back, and the highest of them advances the
+            // digit's count and clears the word
 #pragma unroll
             for (int i = 0; i < kSegItems; ++i) {
                 const uint32_t j = (uint32_t)(warp * kSegItems * 32 + i * 32 + lane);
                 const bool valid = j < my_n;
                 const uint32_t dg = ((k[i] - kbase) >> shift) & 0xffu;
-                uint32_t peers = __ballot_sync(kFullMask, valid);
-#pragma unroll
-                for (int b = 0; b < 8; ++b) {
-                    const bool bit = (dg >> b) & 1u;
-                    const uint32_t bal = __ballot_sync(kFullMask, bit);
-                    peers &= bit ? bal : ~bal;
-                }
+                uint32_t* mw = &s_match[warp * kSegBins + dg];
+                if (valid) atomicOr(mw, 1u << lane);
+                __syncwarp();
+                const uint32_t peers = valid ? *mw : 0u;
                 const uint32_t below = (uint32_t)__popc(peers & lanemask_lt());
                 const uint32_t c = valid ? (uint32_t)s_cnt[warp * kSegBins + dg] : 0u;
                 rank[i] = c + below;
                 __syncwarp();
-                if (valid && below + 1 == (uint32_t)__popc(peers)) s_cnt[warp * kSegBins + dg] = (uint16_t)(c + below + 1);
+                if (valid && below + 1 == (uint32_t)__popc(peers)) {
+                    s_cnt[warp * kSegBins + dg] = (uint16_t)(c + below + 1);
+                    *mw = 0u;
+                }
                 __syncwarp();
             }
             __syncthreads();
@@ -332,6 +348,319 @@ __global__ void __launch_bounds__(kSegThreads, 2) k_seg_cluster(ClusterArgs a) {
     cluster.sync();  // no CTA leaves while others may still read its shared memory
 }
 
+// ---------------------------------------------------------------- split and finish
+
+// Segments above one CTA's worth of keys (8192 < len <= 8 * 8192): a cluster
+// of C CTAs runs ONE count-sort round on the top 8 bits of the segment's key
+// range (the MSD digit), writing the result back to HBM in place (coalesced
+// runs per digit); every warp of the cluster then sorts some of the 256 digit
+// groups (now L2-resident) with BTN in its registers (at most 512 keys, 16 per
+// lane). A digit group above 512 keys is split again on its next 8 bits (a
+// work stack kept identically by every CTA of the cluster), so a group is
+// either finished by a warp, or holds one key value.
+constexpr int kSplitWarpMax = 512;  // longest group a warp finishes (BTN, 16 keys per lane)
+constexpr int kSplitStack = 512;    // pending groups; bound: 4 levels x 65536 / 513
+
+__host__ __device__ constexpr size_t split_smem_bytes(bool vals, int bins) {
+    return (size_t)kSegChunk * 4 * (vals ? 2 : 1)  // staging
+           + (size_t)kSegWarps * bins * 2           // per-warp digit counts
+           + (size_t)kSegWarps * bins * 4           // per-warp peer masks
+           + (size_t)bins * 4 * 5 + 4 * 4           // cta totals, earlier CTAs, base, local start, starts[bins+1]
+           + 64 * 4                                 // misc
+           + (size_t)kSplitStack * 13;              // work stack
+}
+
+// Exclusive scan of a[0..BINS-1] in place (threads 0..BINS-1, BINS <= 512;
+// every thread calls).
+template <int BINS>
+__device__ __forceinline__ void scan_bins(uint32_t* a, uint32_t* wsum) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t x0 = 0, x = 0;
+    if (tid < BINS) {
+        x0 = a[tid];
+        x = x0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFullMask, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+    }
+    __syncthreads();
+    if (tid < BINS) {
+        uint32_t add = 0;
+        for (int w = 0; w < warp; ++w) add += wsum[w];
+        a[tid] = add + x - x0;
+    }
+    __syncthreads();
+}
+
+// One warp sorts a group of 2..512 keys: BTN with B keys per lane, B the
+// smallest power of two with 32 B >= len (all lanes hold keys).
+template <int B>
+__device__ __forceinline__ void btn_warp_fill(uint32_t* k, uint32_t* v, uint32_t len) {
+    int p = 1;
+    while ((uint32_t)(p * B) < len) p <<= 1;
+    net::btn_warp<B>(k, v, len, p);
+}
+
+// The same network on packed 32-bit items: (key - gkb) << ib | index, with
+// ib = bit_length(len) so that every item is below the pad 0xFFFFFFFF (keys
+// only: no index, ib = 0). Needs shift + ib <= 32, shift the bits the group's
+// keys span above gkb.
+template <int B, bool VALS>
+__device__ __forceinline__ void btn_warp_packed(uint32_t* k, uint32_t* v, uint32_t len, uint32_t gkb, int ib) {
+    const int t = threadIdx.x & 31;
+    int p = 1;
+    while ((uint32_t)(p * B) < len) p <<= 1;
+    uint32_t x[B];
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+        const uint32_t g = (uint32_t)t * B + i;
+        x[i] = g < len ? (((k[g] - gkb) << ib) | (VALS ? g : 0u)) : 0xFFFFFFFFu;
+    }
+    net::local_sort<B, uint32_t>(x);
+    for (int kk = 2; kk <= p; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            const bool asc = (t & kk) == 0;
+            const bool lower = t < (t ^ j);
+            net::merge_split_shfl<B, uint32_t>(x, j, lower == asc);
+            net::bitonic_merge<B, uint32_t>(x);
+        }
+    }
+    uint32_t vv[B];
+    if constexpr (VALS) {
+        const uint32_t m = (1u << ib) - 1u;
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+            const uint32_t g = (uint32_t)t * B + i;
+            vv[i] = g < len ? v[x[i] & m] : 0u;
+        }
+    }
+    __syncwarp();  // every payload is read before any is written
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+        const uint32_t g = (uint32_t)t * B + i;
+        if (g < len) {
+            k[g] = gkb + (x[i] >> ib);
+            if constexpr (VALS) v[g] = vv[i];
+        }
+    }
+}
+
+template <bool VALS>
+__device__ __forceinline__ void finish_group_warp(uint32_t* k, uint32_t* v, uint32_t len, uint32_t gkb, int shift) {
+    const int ib = VALS ? 32 - __clz(len) : 0;
+    if (shift + ib <= 32) {
+        if (len <= 32) btn_warp_packed<1, VALS>(k, v, len, gkb, ib);
+        else if (len <= 64) btn_warp_packed<2, VALS>(k, v, len, gkb, ib);
+        else if (len <= 128) btn_warp_packed<4, VALS>(k, v, len, gkb, ib);
+        else if (len <= 256) btn_warp_packed<8, VALS>(k, v, len, gkb, ib);
+        else btn_warp_packed<16, VALS>(k, v, len, gkb, ib);
+        return;
+    }
+    if (len <= 32) btn_warp_fill<1>(k, v, len);
+    else if (len <= 64) btn_warp_fill<2>(k, v, len);
+    else if (len <= 128) btn_warp_fill<4>(k, v, len);
+    else if (len <= 256) btn_warp_fill<8>(k, v, len);
+    else btn_warp_fill<16>(k, v, len);
+}
+
+// RB: the split's digit width (8, or 9 where groups of about 128 keys let
+// payload items pack into 32 bits).
+template <int C, bool VALS, int RB>
+__global__ void __launch_bounds__(kSegThreads, RB == 8 ? 2 : 1) k_seg_split(ClusterArgs a) {
+    constexpr int BINS = 1 << RB;
+    static_assert(BINS <= kSegThreads, "one thread per digit");
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t* s_keys = reinterpret_cast<uint32_t*>(smem);
+    uint32_t* s_vals = s_keys + kSegChunk;
+    uint16_t* s_cnt = reinterpret_cast<uint16_t*>(s_keys + kSegChunk * (VALS ? 2 : 1));
+    uint32_t* s_match = reinterpret_cast<uint32_t*>(s_cnt + kSegWarps * BINS);
+    uint32_t* s_cta = s_match + kSegWarps * BINS;  // this CTA's digit totals
+    uint32_t* s_pre = s_cta + BINS;                 // the digit's keys in lower-ranked CTAs
+    uint32_t* s_base = s_pre + BINS;                // group-relative output start of this CTA's run
+    uint32_t* s_lst = s_base + BINS;                // local start of the digit in the staging buffer
+    uint32_t* s_start = s_lst + BINS;               // [BINS+1] group-relative digit starts (same in every CTA)
+    uint32_t* s_misc = s_start + BINS + 4;          // [1] range flag, [2] stack size, [8..23] warp sums
+    uint32_t* st_lo = s_misc + 64;                      // work stack: group start (segment-relative)
+    uint32_t* st_len = st_lo + kSplitStack;
+    uint32_t* st_kb = st_len + kSplitStack;
+    uint8_t* st_bits = reinterpret_cast<uint8_t*>(st_kb + kSplitStack);
+    if ((size_t)(st_bits + kSplitStack - smem) > dynamic_smem_size()) {
+        if (threadIdx.x == 0) set_status(&a.ctl->status, kStatBounds);
+        return;  // every CTA of the cluster sees the same size: all leave
+    }
+
+    cg::cluster_group cluster = cg::this_cluster();
+    const uint32_t r = C == 1 ? 0u : cluster.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t cnt = a.ctl->counts[a.cls];
+    for (int i = tid; i < kSegWarps * BINS; i += kSegThreads) {
+        s_cnt[i] = 0;
+        s_match[i] = 0;
+    }
+    __syncthreads();
+
+    const uint32_t nclusters = gridDim.x / C;
+    for (uint32_t q = blockIdx.x / C; q < cnt; q += nclusters) {
+        const uint32_t s = a.list[q];
+        const uint64_t seg0 = a.off[s];
+        const uint32_t L = (uint32_t)(a.off[s + 1] - seg0);
+        const int check_bits = a.seg_bits ? 32 : a.key_bits;
+        if (tid == 0) {
+            st_lo[0] = 0;
+            st_len[0] = L;
+            st_kb[0] = a.seg_lo ? a.seg_lo[s] : 0u;
+            st_bits[0] = (uint8_t)(a.seg_bits ? (int)a.seg_bits[s] : a.key_bits);
+            s_misc[2] = 1;
+        }
+        __syncthreads();
+        bool first = true;
+        while (s_misc[2] > 0) {
+            // pop (identically in every CTA)
+            const uint32_t top = s_misc[2] - 1;
+            const uint32_t g_lo = st_lo[top], g_len = st_len[top], kb = st_kb[top];
+            const int bits = st_bits[top];
+            __syncthreads();
+            if (tid == 0) s_misc[2] = top;
+            const int shift = bits > RB ? bits - RB : 0;
+            const uint32_t my_lo = r * (uint32_t)kSegChunk;
+            const uint32_t my_n = g_len > my_lo ? min(g_len - my_lo, (uint32_t)kSegChunk) : 0u;
+            uint32_t* gk = a.keys + seg0 + g_lo;
+            uint32_t* gv = VALS ? a.vals + seg0 + g_lo : nullptr;
+
+            uint32_t k[kSegItems], v[kSegItems], rank[kSegItems];
+            uint32_t orv = 0;
+#pragma unroll
+            for (int i = 0; i < kSegItems; ++i) {
+                const uint32_t j = (uint32_t)(warp * kSegItems * 32 + i * 32 + lane);
+                k[i] = j < my_n ? gk[my_lo + j] : 0u;
+                if constexpr (VALS) v[i] = j < my_n ? gv[my_lo + j] : 0u;
+                orv |= k[i];
+            }
+            if (first) {
+                const int bad = __syncthreads_or(check_bits < 32 && (orv >> check_bits) != 0);
+                if (tid == 0) s_misc[1] = (uint32_t)bad;
+            }
+            // rank among equal digits of the warp, in input order (peer masks)
+#pragma unroll
+            for (int i = 0; i < kSegItems; ++i) {
+                const uint32_t j = (uint32_t)(warp * kSegItems * 32 + i * 32 + lane);
+                const bool valid = j < my_n;
+                const uint32_t dg = ((k[i] - kb) >> shift) & (uint32_t)(BINS - 1);
+                uint32_t* mw = &s_match[warp * BINS + dg];
+                if (valid) atomicOr(mw, 1u << lane);
+                __syncwarp();
+                const uint32_t peers = valid ? *mw : 0u;
+                const uint32_t below = (uint32_t)__popc(peers & lanemask_lt());
+                const uint32_t c = valid ? (uint32_t)s_cnt[warp * BINS + dg] : 0u;
+                rank[i] = c + below;
+                __syncwarp();
+                if (valid && below + 1 == (uint32_t)__popc(peers)) {
+                    s_cnt[warp * BINS + dg] = (uint16_t)(c + below + 1);
+                    *mw = 0u;
+                }
+                __syncwarp();
+            }
+            __syncthreads();
+            if (tid < BINS) {  // per-warp counts -> per-warp exclusive prefixes; CTA totals
+                uint32_t sum = 0;
+#pragma unroll 4
+                for (int w = 0; w < kSegWarps; ++w) {
+                    const uint32_t c = s_cnt[w * BINS + tid];
+                    s_cnt[w * BINS + tid] = (uint16_t)sum;
+                    sum += c;
+                }
+                s_cta[tid] = sum;
+                s_lst[tid] = sum;
+            }
+            cluster.sync();  // (A) every CTA's totals and range flag are visible
+            if (first && check_bits < 32) {
+                uint32_t any = 0;
+                for (int rr = 0; rr < C; ++rr) any |= C == 1 ? s_misc[1] : *cluster.map_shared_rank(&s_misc[1], rr);
+                if (any) {  // the whole cluster leaves the segment unchanged
+                    if (tid == 0 && r == 0) set_status(&a.ctl->status, kStatKeyRange);
+                    for (int i = tid; i < kSegWarps * BINS; i += kSegThreads) s_cnt[i] = 0;
+                    if (tid == 0) s_misc[2] = 0;
+                    cluster.sync();  // no CTA moves on while another reads its flag
+                    break;
+                }
+            }
+            first = false;
+            if (tid < BINS) {
+                uint32_t tot = 0, pre = 0;
+#pragma unroll
+                for (int rr = 0; rr < C; ++rr) {
+                    const uint32_t c = C == 1 ? s_cta[tid] : *cluster.map_shared_rank(&s_cta[tid], rr);
+                    tot += c;
+                    if constexpr (C > 1) pre += (uint32_t)rr < r ? c : 0u;
+                }
+                s_pre[tid] = pre;
+                s_start[tid] = tot;
+            }
+            scan_bins<BINS>(s_start, s_misc + 8);  // group digit starts
+            scan_bins<BINS>(s_lst, s_misc + 8);    // local digit starts
+            if (tid < BINS) s_base[tid] = s_start[tid] + s_pre[tid];
+            if (tid == 0) s_start[BINS] = g_len;
+            // stage by digit (stable), then write runs
+#pragma unroll
+            for (int i = 0; i < kSegItems; ++i) {
+                const uint32_t j = (uint32_t)(warp * kSegItems * 32 + i * 32 + lane);
+                if (j < my_n) {
+                    const uint32_t dg = ((k[i] - kb) >> shift) & (uint32_t)(BINS - 1);
+                    const uint32_t p = s_lst[dg] + s_cnt[warp * BINS + dg] + rank[i];
+                    s_keys[p] = k[i];
+                    if constexpr (VALS) s_vals[p] = v[i];
+                }
+            }
+            __syncthreads();
+            for (uint32_t j = tid; j < my_n; j += kSegThreads) {
+                const uint32_t key = s_keys[j];
+                const uint32_t dg = ((key - kb) >> shift) & (uint32_t)(BINS - 1);
+                const uint32_t o = s_base[dg] + (j - s_lst[dg]);
+                gk[o] = key;
+                if constexpr (VALS) gv[o] = s_vals[j];
+            }
+            for (int i = tid; i < kSegWarps * BINS; i += kSegThreads) s_cnt[i] = 0;
+            cluster.sync();  // (B) the whole group is written
+            // finish the digit groups: warps take groups, larger ones are pushed
+            if (shift > 0) {
+                for (int d = (int)r * kSegWarps + warp; d < BINS; d += C * kSegWarps) {
+                    const uint32_t c0 = s_start[d], c1 = s_start[d + 1], len = c1 - c0;
+                    if (len <= 1 || len > (uint32_t)kSplitWarpMax) continue;
+                    finish_group_warp<VALS>(gk + c0, VALS ? gv + c0 : nullptr, len, kb + ((uint32_t)d << shift),
+                                            shift);
+                }
+                if (warp == 0) {  // push the groups above a warp's reach, in digit order
+                    uint32_t top2 = s_misc[2];
+                    for (int d0 = 0; d0 < BINS; d0 += 32) {
+                        const int d = d0 + lane;
+                        const uint32_t len = s_start[d + 1] - s_start[d];
+                        const bool big = len > (uint32_t)kSplitWarpMax;
+                        const uint32_t m = __ballot_sync(kFullMask, big);
+                        const uint32_t slot = top2 + (uint32_t)__popc(m & lanemask_lt());
+                        if (big) {
+                            if (slot < (uint32_t)kSplitStack) {
+                                st_lo[slot] = g_lo + s_start[d];
+                                st_len[slot] = len;
+                                st_kb[slot] = kb + ((uint32_t)d << shift);
+                                st_bits[slot] = (uint8_t)shift;
+                            } else {  // cannot happen (see kSplitStack)
+                                set_status(&a.ctl->status, kStatBounds);
+                            }
+                        }
+                        top2 = min(top2 + (uint32_t)__popc(m), (uint32_t)kSplitStack);
+                    }
+                    if (lane == 0) s_misc[2] = top2;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    cluster.sync();  // no CTA leaves while others may still read its shared memory
+}
+
 // ---------------------------------------------------------------- host side
 
 struct Tuned {
@@ -369,6 +698,45 @@ isort_status launch_cluster(bool vals, const ClusterArgs& a, cudaStream_t s) {
     return ISORT_OK;
 }
 
+template <int P>
+isort_status launch_btn_cta(uint32_t* keys, uint32_t* vals, const uint64_t* off, uint32_t* lists, uint32_t nseg,
+                            SegCtl* ctl, int cls, uint32_t range_mask, cudaStream_t s) {
+    int per_sm = 0;
+    ISORT_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seg_btn_cta<P>, P, 0));
+    k_seg_btn_cta<P><<<std::max(1, per_sm) * sm_count(), P, 0, s>>>(keys, vals, off, lists + (size_t)cls * nseg, ctl,
+                                                                     cls, range_mask);
+    return from_cuda(cudaGetLastError());
+}
+
+template <int C>
+isort_status launch_split(bool vals, const ClusterArgs& a, cudaStream_t s) {
+    // payload groups pack into 32-bit items when the index fits next to the
+    // key's remaining bits: 9-bit digits for the largest segments
+    constexpr int kRbVals = C == 8 ? 9 : 8;
+    const size_t smem = split_smem_bytes(vals, vals ? 1 << kRbVals : 256);
+    auto kern = vals ? k_seg_split<C, true, kRbVals> : k_seg_split<C, false, 8>;
+    ISORT_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.blockDim = dim3(kSegThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    cfg.gridDim = dim3(C);
+    ISORT_TRY_CUDA(cudaOccupancyMaxActiveClusters(&clusters, (void*)kern, &cfg));
+    if (clusters < 1) return ISORT_ERR_UNSUPPORTED;
+    cfg.gridDim = dim3(C * clusters);
+    LaunchScope ls(C == 2 ? "seg_split2" : C == 4 ? "seg_split4" : "seg_split8", s);
+    ISORT_TRY_CUDA(cudaLaunchKernelEx(&cfg, kern, a));
+    return ISORT_OK;
+}
+
 // Enqueues classification and every class kernel on `s`.
 isort_status enqueue_segmented(uint32_t* keys, uint32_t* vals, const uint64_t* off, uint32_t nseg, int key_bits,
                                SegCtl* ctl, uint32_t* lists, int big_ok, cudaStream_t s,
@@ -396,31 +764,33 @@ isort_status enqueue_segmented(uint32_t* keys, uint32_t* vals, const uint64_t* o
     for (int c : order) {
         a.cls = c;
         a.list = lists + (size_t)c * nseg;
-        isort_status st = c == kClsC8   ? launch_cluster<8>(v, a, s)
-                          : c == kClsC4 ? launch_cluster<4>(v, a, s)
-                          : c == kClsC2 ? launch_cluster<2>(v, a, s)
+        isort_status st = c == kClsC8   ? launch_split<8>(v, a, s)
+                          : c == kClsC4 ? launch_split<4>(v, a, s)
+                          : c == kClsC2 ? launch_split<2>(v, a, s)
                                         : launch_cluster<1>(v, a, s);
         if (st != ISORT_OK) return st;
     }
     {
-        const size_t smem = (size_t)8 * 512 * 8;
-        ISORT_TRY_CUDA(cudaFuncSetAttribute(k_seg_btn_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int per_sm = 0;
-        ISORT_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seg_btn_cta, 512, smem));
         LaunchScope ls("seg_btn_cta", s);
-        k_seg_btn_cta<<<std::max(1, per_sm) * sm_count(), 512, smem, s>>>(keys, vals, off, lists + (size_t)kClsBtnCta * nseg,
-                                                                         ctl, kClsBtnCta, range_mask);
-        ISORT_TRY_CUDA(cudaGetLastError());
+        ISORT_TRY(launch_btn_cta<512>(keys, vals, off, lists, nseg, ctl, kClsCta512, range_mask, s));
+        ISORT_TRY(launch_btn_cta<256>(keys, vals, off, lists, nseg, ctl, kClsCta256, range_mask, s));
+        ISORT_TRY(launch_btn_cta<128>(keys, vals, off, lists, nseg, ctl, kClsCta128, range_mask, s));
+        ISORT_TRY(launch_btn_cta<64>(keys, vals, off, lists, nseg, ctl, kClsCta64, range_mask, s));
     }
     {
+        int per_sm = 0;
+        ISORT_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seg_warp<false>, 256, 0));
         LaunchScope ls("seg_btn_warp", s);
-        k_seg_warp<false><<<4 * sm_count(), 256, 0, s>>>(keys, vals, off, lists + (size_t)kClsBtnWarp * nseg, ctl,
-                                                        kClsBtnWarp, range_mask);
+        k_seg_warp<false><<<std::max(1, per_sm) * sm_count(), 256, 0, s>>>(
+            keys, vals, off, lists + (size_t)kClsBtnWarp * nseg, ctl, kClsBtnWarp, range_mask);
         ISORT_TRY_CUDA(cudaGetLastError());
     }
     {
+        int per_sm = 0;
+        ISORT_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seg_warp<true>, 256, 0));
         LaunchScope ls("seg_oet_warp", s);
-        k_seg_warp<true><<<4 * sm_count(), 256, 0, s>>>(keys, vals, off, lists + (size_t)kClsOet * nseg, ctl, kClsOet, range_mask);
+        k_seg_warp<true><<<std::max(1, per_sm) * sm_count(), 256, 0, s>>>(keys, vals, off, lists + (size_t)kClsOet * nseg,
+                                                                          ctl, kClsOet, range_mask);
         ISORT_TRY_CUDA(cudaGetLastError());
     }
     return ISORT_OK;

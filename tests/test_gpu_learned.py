@@ -70,6 +70,13 @@ def test_learned_sizes_and_bucket_counts(cuda_lib, n, nb):
     assert st["fell_back_to_lsd"] == (1 if n < (1 << 18) else 0)
 
 
+def test_learned_auto_bucket_count(cuda_lib):
+    """nbuckets = 0: 4096 doubled while n / nbuckets > 16384."""
+    keys = _keys("gmm", (1 << 26) + 5, seed=13)
+    st = _learned_vs_oracle(cuda_lib, keys, vals=False, nbuckets=0)
+    assert st["nbuckets"] == 8192 and not st["fell_back_to_lsd"]
+
+
 def test_learned_one_key_value_falls_back(cuda_lib):
     keys = np.full(1 << 19, 0xDEADBEEF, np.uint32)
     st = _learned_vs_oracle(cuda_lib, keys)

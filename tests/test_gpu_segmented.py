@@ -63,6 +63,17 @@ def test_random_lengths(cuda_lib, seed):
     check(cuda_lib, keys, vals, off)
 
 
+@pytest.mark.parametrize("span", [1, 7, 300, 5000, 1 << 20])
+def test_long_segments_narrow_key_ranges(cuda_lib, span):
+    """Segments of 8193..65536 keys whose keys fall in a narrow range, so that
+    the MSD digit groups stay large and are split again (several levels)."""
+    lengths = [8193, 12000, 16385, 30000, 32769, 50000, 65536]
+    keys, vals, off = make(lengths, 40 + span % 97)
+    keys = (np.uint32(123456789) + keys % np.uint32(span)).astype(np.uint32)
+    check(cuda_lib, keys, vals, off)
+    check(cuda_lib, keys, None, off)
+
+
 @pytest.mark.parametrize("key_bits", [8, 16, 20, 31])
 def test_key_bits(cuda_lib, key_bits):
     lengths = [17, 200, 3000, 9000, 20000, 40000, 70000]
