@@ -163,11 +163,12 @@ ISORT_API isort_status isort_segmented(uint32_t* keys, uint32_t* vals, const uin
  *      (256 segments; knots X_0..X_256 and values Y_0..Y_256 are normalised
  *      cumulative sums of softplus(theta), so F is monotone by construction;
  *      knots start at the sample's quantiles) by 64 Adam steps on
- *      (1/m) sum_i (F(u_i) - (i + 1/2)/m)^2, on the GPU;
- *   3. derives an integer splitter table s_1..s_{B-1} (s_b = the first key
- *      with F(key) >= b/B, then made non-decreasing) and assigns every key the
- *      bucket #{b : s_b <= key}; the model proposes floor(F(u) B) and the
- *      splitters confirm or correct it;
+ *      (1/m) sum_i (F(u_i) - (i + 1/2)/m)^2 over every 4th point of the
+ *      sorted sample (m = 2^14), on the GPU;
+ *   3. gives every key the bucket min(B - 1, floor(F(u) B)), F evaluated in a
+ *      fixed fp32 order and clamped to each segment's value range, which makes
+ *      the bucket monotone in the key (buckets are key ranges); the splitter
+ *      table s_b = the first key of bucket b gives each bucket's key range;
  *   4. distributes the keys stably by bucket and sorts every bucket on chip on
  *      the bits its key range spans (a bucket of one key value is skipped).
  * The output is the stable sort of the input, whatever the model learned.
@@ -184,7 +185,7 @@ ISORT_API isort_status isort_segmented(uint32_t* keys, uint32_t* vals, const uin
 typedef struct {
     double imbalance_max_over_mean; /* largest bucket / (n / nbuckets) */
     double overflow_fraction;       /* keys in buckets over 65,536 keys / n */
-    uint64_t fixups;                /* keys whose proposed bucket the splitters corrected */
+    uint64_t fixups;                /* 0: the bucket function needs no corrections (kept for layout) */
     uint64_t overflow_buckets;      /* buckets over 65,536 keys */
     int fell_back_to_lsd;           /* 1: sorted by the plain rounds */
     int train_steps;
@@ -208,10 +209,9 @@ ISORT_API isort_status isort_learned(uint32_t* keys, uint32_t* vals, size_t n, i
  *   loss (device, 1) receive them.
  * isort_cdf_splitters: the splitter table of step 3 from X, Y (device, 257
  *   floats each): splitters (device, nbuckets entries of key_width bits,
- *   nbuckets 2..65536; entry 0 is 0).
- * isort_bucket_ids: the bucket of every key (device, key_width 32 or 64) given
- *   X, Y and the splitter table (nbuckets 2..16384); ids (device, n uint32,
- *   n < 2^32).
+ *   nbuckets 2..65536; entry 0 is 0; s_b = the first key of bucket b).
+ * isort_bucket_ids: the bucket of step 3 of every key (device, key_width 32
+ *   or 64) given X, Y (nbuckets 2..65536); ids (device, n uint32, n < 2^32).
  */
 ISORT_API isort_status isort_cdf_train(const uint32_t* sorted_sample, uint32_t m, int key_bits, float* theta, float* X,
                                        float* Y, float* losses, void* stream);
@@ -220,8 +220,7 @@ ISORT_API isort_status isort_cdf_loss_grad(const float* u, uint32_t m, const flo
 ISORT_API isort_status isort_cdf_splitters(const float* X, const float* Y, int key_width, int key_bits, int nbuckets,
                                            void* splitters, void* stream);
 ISORT_API isort_status isort_bucket_ids(const void* keys, int key_width, size_t n, int key_bits, const float* X,
-                                        const float* Y, const void* splitters, int nbuckets, uint32_t* ids,
-                                        void* stream);
+                                        const float* Y, int nbuckets, uint32_t* ids, void* stream);
 
 /* ---------------------------------------------------------------------------
  * isort_radix_noalloc: isort_radix (in place, u32 keys, optional u32 payload)

@@ -69,11 +69,11 @@ def _lib(mutant: int = 0):
                 getattr(h, nm).restype = u64
             h.oracle_sample_indices.argtypes = [u64, ctypes.c_uint32, u64, vp]
             h.oracle_sample_indices.restype = None
-            h.oracle_pwl_eval_f32.argtypes = [vp, vp, ctypes.c_float]
-            h.oracle_pwl_eval_f32.restype = ctypes.c_float
+            h.oracle_bucket_of.argtypes = [vp, vp, i32, i32, i32, u64]
+            h.oracle_bucket_of.restype = ctypes.c_uint32
             h.oracle_splitters.argtypes = [vp, vp, i32, i32, i32, vp]
             h.oracle_splitters.restype = None
-            h.oracle_bucket_ids.argtypes = [vp, i32, sz, vp, i32, vp]
+            h.oracle_bucket_ids.argtypes = [vp, i32, sz, i32, vp, vp, i32, vp]
             h.oracle_bucket_ids.restype = None
             h.oracle_cdf_knots.argtypes = [vp, vp, vp]
             h.oracle_cdf_knots.restype = None
@@ -213,14 +213,16 @@ def sample_indices(n: int, m: int = SAMPLE_SIZE, seed: int = SAMPLE_SEED):
     return idx
 
 
-def pwl_eval_f32(X, Y, u: float) -> float:
+def bucket_of(X, Y, key: int, key_width: int = 32, key_bits: int = 32, nbuckets: int = 4096) -> int:
+    """The model's bucket of one key."""
     X = np.ascontiguousarray(X, dtype=np.float32)
     Y = np.ascontiguousarray(Y, dtype=np.float32)
-    return float(_lib().oracle_pwl_eval_f32(_p(X), _p(Y), float(np.float32(u))))
+    return int(_lib().oracle_bucket_of(_p(X), _p(Y), key_width, key_bits, nbuckets, int(key)))
 
 
 def splitters(X, Y, key_width: int = 32, key_bits: int = 32, nbuckets: int = 4096):
-    """The splitter table (uint64, nbuckets entries; entry 0 is 0)."""
+    """The splitter table: the first key of each bucket (uint64, nbuckets
+    entries; entry 0 is 0)."""
     X = np.ascontiguousarray(X, dtype=np.float32)
     Y = np.ascontiguousarray(Y, dtype=np.float32)
     s = np.zeros(nbuckets, np.uint64)
@@ -228,12 +230,14 @@ def splitters(X, Y, key_width: int = 32, key_bits: int = 32, nbuckets: int = 409
     return s
 
 
-def bucket_ids(keys, split):
+def bucket_ids(keys, X, Y, key_bits: int = 0, nbuckets: int = 4096):
+    """The model's bucket of every key (uint32)."""
     k = np.ascontiguousarray(keys)
     w = 32 if k.dtype == np.uint32 else 64
-    s = np.ascontiguousarray(split, dtype=np.uint64)
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    Y = np.ascontiguousarray(Y, dtype=np.float32)
     ids = np.empty(k.size, np.uint32)
-    _lib().oracle_bucket_ids(_p(k), w, k.size, _p(s), s.size, _p(ids))
+    _lib().oracle_bucket_ids(_p(k), w, k.size, key_bits or w, _p(X), _p(Y), nbuckets, _p(ids))
     return ids
 
 

@@ -373,62 +373,79 @@ void oracle_sample_indices(uint64_t n, uint32_t m, uint64_t seed, uint64_t* idx)
     }
 }
 
-/* F(u) in float, every operation rounded to nearest in this order:
- * j = the largest j < 256 with X[j] <= u; w = (u - X[j]) / (X[j+1] - X[j]);
- * F = Y[j] + (Y[j+1] - Y[j]) * w, clamped to [0, 1]; u >= X[256] gives Y[256]. */
-static float pwl_eval_f32(const float* X, const float* Y, float u) {
-    if (!(u < X[PWL_SEG])) return Y[PWL_SEG];
+/* The bucket model in float, every operation rounded to nearest in this order
+ * (the definition the sort uses; monotone in the key by construction):
+ *   u = float(key) * 2^-kb;
+ *   j = the largest j < 256 with X[j] <= u (j = 255 when u >= X[256]);
+ *   slope_j = (Y[j+1] - Y[j]) / (X[j+1] - X[j]), 0 when X[j+1] = X[j],
+ *             at most 1e30;
+ *   f = Y[j] + (u - X[j]) * slope_j, then clamped to [Y[j], Y[j+1]];
+ *   bucket = min(B - 1, trunc(f * B)).
+ * Within a segment f grows with u (each operation is monotone) and the clamp
+ * keeps segment j below segment j+1, so the bucket never decreases as the key
+ * grows. */
+static int pwl_segment_f32(const float* X, float u) {
+    if (!(u < X[PWL_SEG])) return PWL_SEG - 1;
     int lo = 0, hi = PWL_SEG;
     while (hi - lo > 1) {
         int mid = (lo + hi) / 2;
         if (X[mid] <= u) lo = mid;
         else hi = mid;
     }
-    float dx = X[lo + 1] - X[lo];
-    float w = dx > 0.f ? (u - X[lo]) / dx : 0.f;
-    float f = Y[lo] + (Y[lo + 1] - Y[lo]) * w;
-    return f < 0.f ? 0.f : (f > 1.f ? 1.f : f);
+    return lo;
 }
 
-float oracle_pwl_eval_f32(const float* X, const float* Y, float u) { return pwl_eval_f32(X, Y, u); }
+static float pwl_slope_f32(const float* X, const float* Y, int j) {
+    float dx = X[j + 1] - X[j];
+    if (!(dx > 0.f)) return 0.f;
+    float sl = (Y[j + 1] - Y[j]) / dx;
+    return sl < 1e30f ? sl : 1e30f;
+}
 
 static float norm_key(uint64_t k, int key_width, float scale) {
     float fk = key_width == 32 ? (float)(uint32_t)k : (float)k;
     return fk * scale;
 }
 
-/* Splitter table: s_0 = 0; for b = 1..B-1, s_b = the first key in [0, 2^kb)
- * with F(key * 2^-kb) >= b/B (the largest key if none), found by bisection;
- * then s_b = max(s_b, s_{b-1}). */
+static uint32_t bucket_model(const float* X, const float* Y, int B, float u) {
+    int j = pwl_segment_f32(X, u);
+    float sl = pwl_slope_f32(X, Y, j);
+    float f = Y[j] + (u - X[j]) * sl;
+    if (f < Y[j]) f = Y[j];
+    if (f > Y[j + 1]) f = Y[j + 1];
+    float fb = f * (float)B;
+    uint32_t b = (uint32_t)fb; /* f >= 0: truncation is the floor */
+    return b > (uint32_t)(B - 1) ? (uint32_t)(B - 1) : b;
+}
+
+uint32_t oracle_bucket_of(const float* X, const float* Y, int key_width, int key_bits, int B, uint64_t key) {
+    return bucket_model(X, Y, B, norm_key(key, key_width, ldexpf(1.0f, -key_bits)));
+}
+
+/* The model's bucket of every key. */
+void oracle_bucket_ids(const void* keys, int key_width, size_t n, int key_bits, const float* X, const float* Y,
+                       int B, uint32_t* ids) {
+    float scale = ldexpf(1.0f, -key_bits);
+    for (size_t i = 0; i < n; ++i) {
+        uint64_t k = key_width == 32 ? (uint64_t)((const uint32_t*)keys)[i] : ((const uint64_t*)keys)[i];
+        ids[i] = bucket_model(X, Y, B, norm_key(k, key_width, scale));
+    }
+}
+
+/* Splitter table (the buckets' lower key bounds): s_0 = 0; for b = 1..B-1,
+ * s_b = the first key in [0, 2^kb) whose bucket is at least b (the largest key
+ * if none), by bisection over the keys. */
 void oracle_splitters(const float* X, const float* Y, int key_width, int key_bits, int B, uint64_t* s) {
     float scale = ldexpf(1.0f, -key_bits);
     s[0] = 0;
     for (int b = 1; b < B; ++b) {
-        float target = (float)b / (float)B;
         uint64_t lo = 0, hi = key_bits >= 64 ? ~0ULL : ((1ULL << key_bits) - 1ULL);
         while (lo < hi) {
             uint64_t mid = lo + ((hi - lo) >> 1);
-            if (pwl_eval_f32(X, Y, norm_key(mid, key_width, scale)) >= target) hi = mid;
+            if (bucket_model(X, Y, B, norm_key(mid, key_width, scale)) >= (uint32_t)b) hi = mid;
             else lo = mid + 1;
         }
         s[b] = lo;
-    }
-    for (int b = 1; b < B; ++b)
-        if (s[b] < s[b - 1]) s[b] = s[b - 1];
-}
-
-/* bucket(key) = #{b in 1..B-1 : s_b <= key}. */
-void oracle_bucket_ids(const void* keys, int key_width, size_t n, const uint64_t* s, int B, uint32_t* ids) {
-    for (size_t i = 0; i < n; ++i) {
-        uint64_t k = key_width == 32 ? (uint64_t)((const uint32_t*)keys)[i] : ((const uint64_t*)keys)[i];
-        /* s_1..s_{B-1} is non-decreasing: count the entries <= k by bisection */
-        int lo = 1, hi = B; /* first index in [1, B) with s > k, or B */
-        while (lo < hi) {
-            int mid = (lo + hi) / 2;
-            if (s[mid] <= k) lo = mid + 1;
-            else hi = mid;
-        }
-        ids[i] = (uint32_t)(lo - 1);
     }
 }
 

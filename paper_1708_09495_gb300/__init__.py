@@ -73,7 +73,7 @@ SIGNATURES = [
     ("isort_cdf_train", _i32, [_vp, ctypes.c_uint32, _i32, _vp, _vp, _vp, _vp, _vp]),
     ("isort_cdf_loss_grad", _i32, [_vp, ctypes.c_uint32, _vp, _vp, _vp, _vp]),
     ("isort_cdf_splitters", _i32, [_vp, _vp, _i32, _i32, _i32, _vp, _vp]),
-    ("isort_bucket_ids", _i32, [_vp, _i32, _sz, _i32, _vp, _vp, _vp, _i32, _vp, _vp]),
+    ("isort_bucket_ids", _i32, [_vp, _i32, _sz, _i32, _vp, _vp, _i32, _vp, _vp]),
     ("isort_set_sync", _i32, [_i32]),
     ("isort_device_status", _i32, [_i32, _vp]),
     ("isort_set_spin_limit", _i32, [_u64]),
@@ -288,13 +288,14 @@ def cdf_splitters(X, Y, key_width: int = 32, key_bits: int = 0, nbuckets: int = 
     return out
 
 
-def bucket_ids(keys, X, Y, splitters, key_bits: int = 0, stream=None):
+def bucket_ids(keys, X, Y, nbuckets: int = 4096, key_bits: int = 0, stream=None):
+    """The learned model's bucket of every key (int32 tensor of bucket ids)."""
     import torch
 
     w = _key_width(keys)
     ids = torch.empty(keys.numel(), dtype=torch.int32, device=keys.device)
-    _check(load().isort_bucket_ids(_ptr(keys), w, keys.numel(), key_bits, _ptr(X), _ptr(Y), _ptr(splitters),
-                                   splitters.numel(), _ptr(ids), _stream(stream)), "isort_bucket_ids")
+    _check(load().isort_bucket_ids(_ptr(keys), w, keys.numel(), key_bits, _ptr(X), _ptr(Y), nbuckets, _ptr(ids),
+                                   _stream(stream)), "isort_bucket_ids")
     return ids
 
 

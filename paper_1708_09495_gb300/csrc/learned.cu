@@ -1,7 +1,7 @@
 // Learned-bucket sort: a monotone CDF model, trained on the GPU on a sample
-// that the method sorts itself, proposes each key's bucket for an MSD
-// distribution pass; exact integer splitters fix the proposals up, and the
-// buckets are then finished independently on chip.
+// that the method sorts itself, gives each key its bucket for an MSD
+// distribution (the bucket function is monotone in the key, so buckets are
+// key ranges), and the buckets are then finished independently on chip.
 //
 // There is no counterpart in Gerbessiotis (arXiv:1708.09495). The bucketing
 // grows out of the splitter-based sample sorts the paper discusses (Section 2:
@@ -13,15 +13,15 @@
 //   1. sample m = 2^16 keys at indices drawn from SplitMix64 (Steele, Lea &
 //      Flood 2014), sort them with the library's own radix rounds;
 //   2. train the 256-segment PWL CDF (learned.cuh) by Adam on the mean squared
-//      error between F(u_i) and the sample's empirical CDF (i + 1/2)/m; knot
+//      error between F(u_i) and the empirical CDF (i + 1/2)/m of every 4th
+//      point of the sorted sample (m = 2^14, 64 points per segment); knot
 //      positions start at sample quantiles, values at i/256; all steps run in
 //      one single-CTA kernel, and the parameters with the lowest loss seen
 //      (the initial ones included) are kept;
-//   3. splitter table: s_b = first key with F(key) >= b/B (fp32, fixed
-//      operation order), made non-decreasing; bucket(key) = #{b in 1..B-1 :
-//      s_b <= key}. The model's proposal floor(F(u) B) (F through a segment
-//      table and per-segment slopes) is accepted when the splitters confirm
-//      it, else a binary search fixes it (counted);
+//   3. bucket(key) = min(B - 1, floor(F(u) B)) with F evaluated in a fixed
+//      fp32 order and clamped per segment (learned.cuh), which makes it
+//      monotone in the key; the splitter table s_b = the first key of bucket
+//      b gives each bucket's key range;
 //   4. census: bucket sizes, fix-ups, per-chunk counts for the first pass;
 //      too many keys in buckets beyond the on-chip capacity -> plain LSD;
 //   5. stable distribution by bucket: two stable passes over the bucket id's
@@ -53,6 +53,7 @@ constexpr uint32_t kSampleSize = 1u << 16;
 constexpr uint64_t kSampleSeed = 0x5EED5EED5EEDull;
 constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
 constexpr int kTrainSteps = 64;
+constexpr uint32_t kFitStride = 4;  // the fit sees every 4th point of the sorted sample
 constexpr float kLearningRate = 0.02f;
 constexpr uint32_t kOnChipCapacity = 65536;  // keys a cluster finishes on chip
 constexpr int kMaxBuckets = 16384;           // the splitter table is held in shared memory
@@ -74,10 +75,12 @@ __global__ void k_sample_gather(const K* __restrict__ keys, uint64_t n, uint32_t
     out[j] = keys[idx];
 }
 
+// u[j] = the normalised value of sorted[j * stride + stride / 2], j < m.
 template <typename K>
-__global__ void k_normalise(const K* __restrict__ sorted, uint32_t m, float scale, float* __restrict__ u) {
+__global__ void k_normalise(const K* __restrict__ sorted, uint32_t m, uint32_t stride, float scale,
+                            float* __restrict__ u) {
     const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < m) u[j] = normalise_key(sorted[j], scale);
+    if (j < m) u[j] = normalise_key(sorted[(size_t)j * stride + stride / 2], scale);
 }
 
 // ---------------------------------------------------------------- the model
@@ -327,6 +330,8 @@ __global__ void __launch_bounds__(kFitThreads, 1)
 
 // ---------------------------------------------------------------- splitters
 
+// s_0 = 0; s_b = the first key whose bucket is at least b (the largest key if
+// none): the buckets' lower key bounds, by bisection over the keys.
 template <typename K>
 __global__ void k_splitters(const float* __restrict__ X, const float* __restrict__ Y, int B, int key_bits,
                             float scale, K* __restrict__ split) {
@@ -341,78 +346,59 @@ __global__ void k_splitters(const float* __restrict__ X, const float* __restrict
         if (b == 0) split[0] = 0;
         return;
     }
-    const float target = __fdiv_rn(__int2float_rn(b), __int2float_rn(B));
     uint64_t lo = 0, hi = key_bits >= 64 ? ~0ull : ((1ull << key_bits) - 1ull);
-    while (lo < hi) {  // first key with F(key) >= target (the largest key if none)
+    while (lo < hi) {
         const uint64_t mid = lo + ((hi - lo) >> 1);
-        if (pwl_eval(sX, sY, normalise_key((K)mid, scale)) >= target) hi = mid;
+        if (pwl_bucket(sX, sY, normalise_key((K)mid, scale), B) >= (uint32_t)b) hi = mid;
         else lo = mid + 1;
     }
     split[b] = (K)lo;
-}
-
-template <typename K>
-__global__ void k_splitters_monotone(K* split, int B) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    K run = 0;
-    for (int b = 1; b < B; ++b) {
-        if (split[b] < run) split[b] = run;
-        run = split[b];
-    }
 }
 
 // ---------------------------------------------------------------- bucket lookup
 
 constexpr int kSegTable = 1024;  // segment index table over u in [0, 1)
 
-// Shared-memory bytes of a bucket lookup: X, Y, slopes, segment table, splitters.
-__host__ __device__ constexpr size_t bucket_tab_bytes(int B, size_t key_bytes) {
-    return 2 * ((kPwlKnots * 4 + 15) / 16 * 16) + kPwlSegments * 4 + ((kSegTable + 1) + 15) / 16 * 16 +
-           (((size_t)B * key_bytes + 15) / 16 * 16);
+// Shared-memory bytes of a bucket lookup: X, Y, slopes, segment table.
+__host__ __device__ constexpr size_t bucket_tab_bytes() {
+    return 2 * ((kPwlKnots * 4 + 15) / 16 * 16) + kPwlSegments * 4 + ((kSegTable + 1) + 15) / 16 * 16;
 }
 
-// Bucket of a key from the splitter table: #{b in 1..B-1 : s_b <= key}. The
-// model proposes floor(F(u) B) (F evaluated through the segment table and the
-// segment slopes); the splitters accept it, or a bisection over them decides.
-// The result depends on the splitters alone.
+// The bucket model (learned.cuh) with the segment found through a table over
+// u: s_seg[q] = pwl_segment(X, q / kSegTable), so the segment of u lies in
+// [s_seg[q], s_seg[q + 1]] for q = floor(u kSegTable); a bisection there gives
+// pwl_segment(X, u) itself. Slopes are computed once per CTA by pwl_slope.
 template <typename K>
 struct BucketDigit {
     static constexpr bool kCheap = false;
-    const K* g_split;
     const float* g_X;
     const float* g_Y;
     int B;
     float scale;
     int sub_shift;
     uint32_t sub_mask;
-    K* s_split;
     float* s_X;
     float* s_Y;
     float* s_slope;
     uint8_t* s_seg;
-    __device__ __forceinline__ size_t table_bytes() const { return bucket_tab_bytes(B, sizeof(K)); }
+    __device__ __forceinline__ size_t table_bytes() const { return bucket_tab_bytes(); }
     __device__ __forceinline__ void setup(unsigned char* p) {
         constexpr size_t kv = (kPwlKnots * 4 + 15) / 16 * 16;
         s_X = reinterpret_cast<float*>(p);
         s_Y = reinterpret_cast<float*>(p + kv);
         s_slope = reinterpret_cast<float*>(p + 2 * kv);
         s_seg = p + 2 * kv + kPwlSegments * 4;
-        s_split = reinterpret_cast<K*>(p + 2 * kv + kPwlSegments * 4 + ((kSegTable + 1) + 15) / 16 * 16);
         for (int i = threadIdx.x; i < kPwlKnots; i += blockDim.x) {
             s_X[i] = g_X[i];
             s_Y[i] = g_Y[i];
         }
-        for (int i = threadIdx.x; i < B; i += blockDim.x) s_split[i] = g_split[i];
         __syncthreads();
-        for (int j = threadIdx.x; j < kPwlSegments; j += blockDim.x) {
-            const float dx = s_X[j + 1] - s_X[j];
-            s_slope[j] = dx > 0.f ? (s_Y[j + 1] - s_Y[j]) / dx : 0.f;
-        }
+        for (int j = threadIdx.x; j < kPwlSegments; j += blockDim.x) s_slope[j] = pwl_slope(s_X, s_Y, j);
         for (int q = threadIdx.x; q <= kSegTable; q += blockDim.x)
             s_seg[q] = (uint8_t)pwl_segment(s_X, (float)q * (1.f / kSegTable));
         __syncthreads();
     }
-    __device__ __forceinline__ uint32_t bucket(K k, bool* fixed) const {
+    __device__ __forceinline__ uint32_t bucket(K k) const {
         const float u = normalise_key(k, scale);
         const int q = min((int)(u * (float)kSegTable), kSegTable - 1);
         int lo = s_seg[q], hi = s_seg[q + 1];  // lo <= segment(u) <= hi
@@ -421,25 +407,7 @@ struct BucketDigit {
             if (s_X[mid] <= u) lo = mid;
             else hi = mid - 1;
         }
-        const float f = s_Y[lo] + (u - s_X[lo]) * s_slope[lo];
-        int b0 = (int)(f * (float)B);
-        b0 = b0 < 0 ? 0 : (b0 > B - 1 ? B - 1 : b0);
-        if ((b0 == 0 || s_split[b0] <= k) && (b0 == B - 1 || k < s_split[b0 + 1])) {
-            *fixed = false;
-            return (uint32_t)b0;
-        }
-        *fixed = true;
-        int a = 0, c = B - 1;  // largest b with (b == 0 || s_b <= k)
-        while (a < c) {
-            const int mid = (a + c + 1) >> 1;
-            if (s_split[mid] <= k) a = mid;
-            else c = mid - 1;
-        }
-        return (uint32_t)a;
-    }
-    __device__ __forceinline__ uint32_t bucket(K k) const {
-        bool fixed;
-        return bucket(k, &fixed);
+        return pwl_bucket_in(s_X, s_Y, s_slope[lo], lo, u, B);
     }
     __device__ __forceinline__ uint32_t digit(K k) const { return (bucket(k) >> sub_shift) & sub_mask; }
 };
@@ -472,9 +440,9 @@ __device__ __forceinline__ void for_chunk_keys(const K* __restrict__ keys, uint3
     for (uint32_t b = i + threadIdx.x; b < hi; b += blockDim.x) f(b, keys[b]);
 }
 
-// Census: per-chunk counts of the first pass's digit, every bucket's size
-// (global), the number of proposals the splitters corrected, and the key-range
-// check (a key of key_bits or more bits sets the status).
+// Census: per-chunk counts of the first pass's digit, every bucket's size per
+// chunk, and the key-range check (a key of key_bits or more bits sets the
+// status).
 constexpr int kCensusThreads = 512;
 
 template <typename K>
@@ -482,8 +450,7 @@ __global__ void __launch_bounds__(kCensusThreads) k_bucket_census(const K* __res
                                                                   uint32_t chunk_keys, BucketDigit<K> df,
                                                                   uint32_t* __restrict__ hist,
                                                                   uint32_t* __restrict__ bucket_count,
-                                                                  unsigned long long* fixups, int key_bits,
-                                                                  uint32_t* status, int vec) {
+                                                                  int key_bits, uint32_t* status, int vec) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int bins = (int)df.sub_mask + 1;
     uint32_t* s_h = reinterpret_cast<uint32_t*>(smem);             // [bins]
@@ -493,23 +460,27 @@ __global__ void __launch_bounds__(kCensusThreads) k_bucket_census(const K* __res
     for (int i = threadIdx.x; i < df.B; i += kCensusThreads) s_b[i] = 0;
     df.setup(tab);
     const uint32_t lo = blockIdx.x * chunk_keys, hi = min(n, lo + chunk_keys);
-    uint32_t fix = 0;
     K kor = 0;
     for_chunk_keys<K>(keys, lo, hi, vec != 0, [&](uint32_t, K k) {
         kor |= k;
-        bool fixed;
-        const uint32_t b = df.bucket(k, &fixed);
-        fix += fixed ? 1u : 0u;
+        const uint32_t b = df.bucket(k);
         atomicAdd(&s_h[(b >> df.sub_shift) & df.sub_mask], 1u);
         atomicAdd(&s_b[b], 1u);
     });
     __syncthreads();
     for (int i = threadIdx.x; i < bins; i += kCensusThreads) hist[(size_t)blockIdx.x * bins + i] = s_h[i];
-    for (int i = threadIdx.x; i < df.B; i += kCensusThreads)
-        if (s_b[i]) atomicAdd(&bucket_count[i], s_b[i]);
-    fix = __reduce_add_sync(kFullMask, fix);
-    if ((threadIdx.x & 31) == 0 && fix) atomicAdd(fixups, (unsigned long long)fix);
+    // this chunk's bucket sizes (summed over chunks by k_sum_columns)
+    for (int i = threadIdx.x; i < df.B; i += kCensusThreads) bucket_count[(size_t)blockIdx.x * df.B + i] = s_b[i];
     if (key_bits < (int)sizeof(K) * 8 && (kor >> key_bits) != 0) set_status(status, kStatKeyRange);
+}
+
+// out[c] = sum over rows r of in[r * cols + c] (fixed order).
+__global__ void k_sum_columns(const uint32_t* __restrict__ in, uint32_t rows, uint32_t cols, uint32_t* __restrict__ out) {
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    uint32_t sum = 0;
+    for (uint32_t r = 0; r < rows; ++r) sum += in[(size_t)r * cols + c];
+    out[c] = sum;
 }
 
 // Per-chunk counts of a later pass's digit.
@@ -518,15 +489,21 @@ __global__ void __launch_bounds__(kCensusThreads) k_bucket_hist(const K* __restr
                                                                 uint32_t chunk_keys, BucketDigit<K> df,
                                                                 uint32_t* __restrict__ hist, int vec) {
     extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int kWarps = kCensusThreads / 32;
     const int bins = (int)df.sub_mask + 1;
-    uint32_t* s_h = reinterpret_cast<uint32_t*>(smem);
-    unsigned char* tab = smem + align_up_dev((size_t)bins * 4, 16);
-    for (int i = threadIdx.x; i < bins; i += kCensusThreads) s_h[i] = 0;
+    uint32_t* s_h = reinterpret_cast<uint32_t*>(smem);  // [kWarps][bins]: one copy per warp
+    unsigned char* tab = smem + align_up_dev((size_t)kWarps * bins * 4, 16);
+    for (int i = threadIdx.x; i < kWarps * bins; i += kCensusThreads) s_h[i] = 0;
     df.setup(tab);
+    uint32_t* my_h = s_h + (threadIdx.x >> 5) * bins;
     const uint32_t lo = blockIdx.x * chunk_keys, hi = min(n, lo + chunk_keys);
-    for_chunk_keys<K>(keys, lo, hi, vec != 0, [&](uint32_t, K k) { atomicAdd(&s_h[df.digit(k)], 1u); });
+    for_chunk_keys<K>(keys, lo, hi, vec != 0, [&](uint32_t, K k) { atomicAdd(&my_h[df.digit(k)], 1u); });
     __syncthreads();
-    for (int i = threadIdx.x; i < bins; i += kCensusThreads) hist[(size_t)blockIdx.x * bins + i] = s_h[i];
+    for (int i = threadIdx.x; i < bins; i += kCensusThreads) {
+        uint32_t c = 0;
+        for (int w = 0; w < kWarps; ++w) c += s_h[w * bins + i];
+        hist[(size_t)blockIdx.x * bins + i] = c;
+    }
 }
 
 // Bucket ids of every key (the distribution passes' lookup, for checking).
@@ -568,7 +545,7 @@ isort_status launch_bucket_sweep(const SweepArgs& a, const BucketDigit<K>& df, u
                                  cudaStream_t s) {
     using Cfg = SweepCfg<K, true, 512, 8>;
     using CfgK = SweepCfg<K, false, 512, 8>;
-    const size_t tb = bucket_tab_bytes(df.B, sizeof(K));
+    const size_t tb = bucket_tab_bytes();
     LaunchScope ls("bucket_sweep", s);
     if (vals) {
         const size_t smem = Cfg::smem_bytes(a.bins, false, tb);
@@ -599,7 +576,7 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
     // launch geometry of the distribution passes
     using Cfg = SweepCfg<K, true, 512, 8>;
     const uint32_t tile = 512 * 8;
-    const size_t tb = bucket_tab_bytes(B, sizeof(K));
+    const size_t tb = bucket_tab_bytes();
     const size_t sweep_smem = Cfg::smem_bytes(bins, false, tb);
     const size_t census_smem = align_up((size_t)bins * 4 + align_up((size_t)B, 4) * 4, 16) + tb;
     if (sweep_smem > max_smem_optin() || census_smem > max_smem_optin()) return ISORT_ERR_UNSUPPORTED;
@@ -622,12 +599,13 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
         off += align_up(bytes, 256);
         return o;
     };
-    const size_t o_status = take(64), o_fix = take(64);
+    const size_t o_status = take(64);
     const size_t o_sample = take((size_t)m * sizeof(K)), o_u = take((size_t)m * 4);
     const size_t o_theta = take(2 * kPwlSegments * 4);
     const size_t o_X = take(kPwlKnots * 4), o_Y = take(kPwlKnots * 4);
     const size_t o_loss = take((kTrainSteps + 2) * 4);
     const size_t o_split = take((size_t)B * sizeof(K)), o_bcount = take((size_t)B * 4);
+    const size_t o_bpart = take((size_t)chunks * B * 4);
     const size_t o_hist = take((size_t)chunks * bins * 4), o_coff = take((size_t)chunks * bins * 4);
     const size_t o_segoff = take((size_t)(B + 1) * 8), o_seglo = take((size_t)B * 4), o_segbits = take((size_t)B);
     const size_t o_buf = take(n * sizeof(K) + (hv ? align_up(n * 4, 256) : 0));
@@ -639,7 +617,6 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
         return e;
     };
     uint32_t* status = reinterpret_cast<uint32_t*>(ws + o_status);
-    unsigned long long* fixups = reinterpret_cast<unsigned long long*>(ws + o_fix);
     K* sample = reinterpret_cast<K*>(ws + o_sample);
     float* u = reinterpret_cast<float*>(ws + o_u);
     float* theta = reinterpret_cast<float*>(ws + o_theta);
@@ -648,6 +625,7 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
     float* losses = reinterpret_cast<float*>(ws + o_loss);
     K* split = reinterpret_cast<K*>(ws + o_split);
     uint32_t* bcount = reinterpret_cast<uint32_t*>(ws + o_bcount);
+    uint32_t* bpart = reinterpret_cast<uint32_t*>(ws + o_bpart);
     uint32_t* hist = reinterpret_cast<uint32_t*>(ws + o_hist);
     uint32_t* coff = reinterpret_cast<uint32_t*>(ws + o_coff);
     uint64_t* segoff = reinterpret_cast<uint64_t*>(ws + o_segoff);
@@ -657,7 +635,6 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
     uint32_t* wv = hv ? reinterpret_cast<uint32_t*>(ws + o_buf + align_up(n * sizeof(K), 256)) : nullptr;
 
     cudaError_t ce = cudaMemsetAsync(ws, 0, 128, s);
-    if (ce == cudaSuccess) ce = cudaMemsetAsync(bcount, 0, (size_t)B * 4, s);
     if (ce != cudaSuccess) return fail(from_cuda(ce));
 
     // 1. sample and sort it
@@ -674,24 +651,22 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
     // 2. train the model
     {
         LaunchScope ls("cdf_init", s);
-        k_normalise<K><<<(m + 255) / 256, 256, 0, s>>>(sample, m, scale, u);
+        k_normalise<K><<<(m / kFitStride + 255) / 256, 256, 0, s>>>(sample, m / kFitStride, kFitStride, scale, u);
         k_model_init<K><<<1, kPwlSegments, 0, s>>>(sample, m, scale, theta);
         ce = cudaGetLastError();
         if (ce != cudaSuccess) return fail(from_cuda(ce));
     }
-    st = launch_fit(u, m, theta, X, Y, losses, nullptr, nullptr, kTrainSteps, s);
+    st = launch_fit(u, m / kFitStride, theta, X, Y, losses, nullptr, nullptr, kTrainSteps, s);
     if (st != ISORT_OK) return fail(st);
 
     // 3. splitters
     {
         LaunchScope ls("splitters", s);
         k_splitters<K><<<(B + 255) / 256, 256, 0, s>>>(X, Y, B, key_bits, scale, split);
-        k_splitters_monotone<K><<<1, 32, 0, s>>>(split, B);
         ce = cudaGetLastError();
         if (ce != cudaSuccess) return fail(from_cuda(ce));
     }
     BucketDigit<K> df;
-    df.g_split = split;
     df.g_X = X;
     df.g_Y = Y;
     df.B = B;
@@ -706,21 +681,20 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
         ce = cudaFuncSetAttribute(k_bucket_census<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (ce != cudaSuccess) return fail(from_cuda(ce));
         LaunchScope ls("bucket_census", s);
-        k_bucket_census<K><<<chunks, kCensusThreads, smem, s>>>(keys, (uint32_t)n, chunk_tiles * tile, df, hist, bcount,
-                                                              fixups, key_bits, status, vec);
+        k_bucket_census<K><<<chunks, kCensusThreads, smem, s>>>(keys, (uint32_t)n, chunk_tiles * tile, df, hist, bpart,
+                                                              key_bits, status, vec);
+        k_sum_columns<<<(B + 255) / 256, 256, 0, s>>>(bpart, chunks, (uint32_t)B, bcount);
         ce = cudaGetLastError();
         if (ce != cudaSuccess) return fail(from_cuda(ce));
     }
     std::vector<uint32_t> h_count(B);
     std::vector<K> h_split(B);
     std::vector<float> h_loss(kTrainSteps + 2);
-    unsigned long long h_fix = 0;
     uint32_t h_status = 0;
     ce = cudaMemcpyAsync(h_count.data(), bcount, (size_t)B * 4, cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(&h_status, status, 4, cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_split.data(), split, (size_t)B * sizeof(K), cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_loss.data(), losses, (kTrainSteps + 2) * 4, cudaMemcpyDeviceToHost, s);
-    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&h_fix, fixups, 8, cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess) return fail(from_cuda(ce));
     if (h_status != 0) return fail(map_bits(h_status));  // keys unchanged
@@ -735,7 +709,7 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
     stats->imbalance_max_over_mean = (double)maxc / ((double)n / B);
     stats->overflow_fraction = (double)over / (double)n;
     stats->overflow_buckets = over_b;
-    stats->fixups = h_fix;
+    stats->fixups = 0;  // the bucket function is monotone: nothing to correct
     stats->train_loss = h_loss[kTrainSteps];
     stats->train_loss_initial = h_loss[kTrainSteps + 1];
     stats->train_steps = kTrainSteps;
@@ -759,7 +733,7 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
         df.sub_mask = (uint32_t)((1 << std::min(wsub, id_bits - p * wsub)) - 1);
         const int pbins = (int)df.sub_mask + 1;
         if (p > 0) {
-            const size_t smem = align_up((size_t)pbins * 4, 16) + tb;
+            const size_t smem = align_up((size_t)(kCensusThreads / 32) * pbins * 4, 16) + tb;
             ce = cudaFuncSetAttribute(k_bucket_hist<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (ce != cudaSuccess) return fail(from_cuda(ce));
             LaunchScope ls("bucket_hist", s);
@@ -892,11 +866,9 @@ isort_status isort_cdf_splitters(const float* X, const float* Y, int key_width, 
     if (key_width == 32) {
         k_splitters<uint32_t><<<(nbuckets + 255) / 256, 256, 0, s>>>(X, Y, nbuckets, key_bits, scale,
                                                                      static_cast<uint32_t*>(splitters));
-        k_splitters_monotone<uint32_t><<<1, 32, 0, s>>>(static_cast<uint32_t*>(splitters), nbuckets);
     } else {
         k_splitters<uint64_t><<<(nbuckets + 255) / 256, 256, 0, s>>>(X, Y, nbuckets, key_bits, scale,
                                                                      static_cast<uint64_t*>(splitters));
-        k_splitters_monotone<uint64_t><<<1, 32, 0, s>>>(static_cast<uint64_t*>(splitters), nbuckets);
     }
     ISORT_TRY_CUDA(cudaGetLastError());
     if (sync_mode()) ISORT_TRY_CUDA(cudaStreamSynchronize(s));
@@ -904,29 +876,22 @@ isort_status isort_cdf_splitters(const float* X, const float* Y, int key_width, 
 }
 
 isort_status isort_bucket_ids(const void* keys, int key_width, size_t n, int key_bits, const float* X, const float* Y,
-                              const void* splitters, int nbuckets, uint32_t* ids, void* stream) {
+                              int nbuckets, uint32_t* ids, void* stream) {
     if (key_width != 32 && key_width != 64) return ISORT_ERR_INVALID_ARG;
     if (key_bits == 0) key_bits = key_width;
-    if (key_bits < 1 || key_bits > key_width || nbuckets < 2 || nbuckets > kMaxBuckets) return ISORT_ERR_INVALID_ARG;
+    if (key_bits < 1 || key_bits > key_width || nbuckets < 2 || nbuckets > 65536) return ISORT_ERR_INVALID_ARG;
     if (n == 0) return ISORT_OK;
-    if (!keys || !X || !Y || !splitters || !ids || n >= (size_t(1) << 32)) return ISORT_ERR_INVALID_ARG;
+    if (!keys || !X || !Y || !ids || n >= (size_t(1) << 32)) return ISORT_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const float scale = std::ldexp(1.0f, -key_bits);
     const unsigned grid = (unsigned)std::min<size_t>((n + 255) / 256, (size_t)sm_count() * 8);
+    const size_t smem = bucket_tab_bytes();
     LaunchScope ls("bucket_ids", s);
     if (key_width == 32) {
-        BucketDigit<uint32_t> df{static_cast<const uint32_t*>(splitters), X, Y, nbuckets, scale, 0, 0xffffu,
-                                 nullptr, nullptr, nullptr, nullptr, nullptr};
-        const size_t smem = bucket_tab_bytes(nbuckets, 4);
-        ISORT_TRY_CUDA(cudaFuncSetAttribute(k_bucket_ids<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)smem));
+        BucketDigit<uint32_t> df{X, Y, nbuckets, scale, 0, 0xffffu, nullptr, nullptr, nullptr, nullptr};
         k_bucket_ids<uint32_t><<<grid, 256, smem, s>>>(static_cast<const uint32_t*>(keys), (uint32_t)n, df, ids);
     } else {
-        BucketDigit<uint64_t> df{static_cast<const uint64_t*>(splitters), X, Y, nbuckets, scale, 0, 0xffffu,
-                                 nullptr, nullptr, nullptr, nullptr, nullptr};
-        const size_t smem = bucket_tab_bytes(nbuckets, 8);
-        ISORT_TRY_CUDA(cudaFuncSetAttribute(k_bucket_ids<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)smem));
+        BucketDigit<uint64_t> df{X, Y, nbuckets, scale, 0, 0xffffu, nullptr, nullptr, nullptr, nullptr};
         k_bucket_ids<uint64_t><<<grid, 256, smem, s>>>(static_cast<const uint64_t*>(keys), (uint32_t)n, df, ids);
     }
     ISORT_TRY_CUDA(cudaGetLastError());
@@ -960,7 +925,7 @@ isort_status isort_cdf_train(const uint32_t* sorted_sample, uint32_t m, int key_
     const float scale = std::ldexp(1.0f, -key_bits);
     {
         LaunchScope ls("cdf_init", s);
-        k_normalise<uint32_t><<<(m + 255) / 256, 256, 0, s>>>(sorted_sample, m, scale, u);
+        k_normalise<uint32_t><<<(m + 255) / 256, 256, 0, s>>>(sorted_sample, m, 1, scale, u);
         k_model_init<uint32_t><<<1, kPwlSegments, 0, s>>>(sorted_sample, m, scale, theta);
         st = from_cuda(cudaGetLastError());
     }

@@ -7,9 +7,10 @@
 // Y_0 = 0 <= Y_1 <= ... <= Y_K = 1, each from K positive increments
 // softplus(theta_i) normalised by their sum (monotone by construction):
 //   F(u) = Y_j + (Y_{j+1} - Y_j) * (u - X_j) / (X_{j+1} - X_j),  X_j <= u < X_{j+1}.
-// Every fp32 operation of F is written with an explicit round-to-nearest
-// intrinsic in a fixed order, so that the splitter table derived from F is a
-// function of (X, Y) alone, reproducible off the GPU.
+// Every fp32 operation of the bucket model is written with an explicit
+// round-to-nearest intrinsic in a fixed order, so that the buckets (and the
+// splitter table derived from them) are a function of (X, Y) alone,
+// reproducible off the GPU.
 #pragma once
 
 #include "common.cuh"
@@ -37,14 +38,31 @@ __device__ __forceinline__ int pwl_segment(const float* X, float u) {
     return lo;
 }
 
-__device__ __forceinline__ float pwl_eval(const float* X, const float* Y, float u) {
-    if (!(u < X[kPwlSegments])) return Y[kPwlSegments];
-    const int j = pwl_segment(X, u);
+// The bucket model (the definition the sort uses), every fp32 operation
+// rounded to nearest in this order:
+//   j = pwl_segment(X, u); slope_j = (Y_{j+1} - Y_j) / (X_{j+1} - X_j) (0 for
+//   an empty segment, at most 1e30); f = Y_j + (u - X_j) slope_j clamped to
+//   [Y_j, Y_{j+1}]; bucket = min(B - 1, trunc(f B)).
+// Each operation is monotone and the clamp keeps segment j below segment j+1,
+// so the bucket never decreases as the key grows: buckets are key ranges.
+__device__ __forceinline__ float pwl_slope(const float* X, const float* Y, int j) {
     const float dx = __fsub_rn(X[j + 1], X[j]);
-    const float w = dx > 0.f ? __fdiv_rn(__fsub_rn(u, X[j]), dx) : 0.f;
-    float f = __fadd_rn(Y[j], __fmul_rn(__fsub_rn(Y[j + 1], Y[j]), w));
-    f = f < 0.f ? 0.f : (f > 1.f ? 1.f : f);
-    return f;
+    if (!(dx > 0.f)) return 0.f;
+    const float sl = __fdiv_rn(__fsub_rn(Y[j + 1], Y[j]), dx);
+    return sl < 1e30f ? sl : 1e30f;
+}
+
+__device__ __forceinline__ uint32_t pwl_bucket_in(const float* X, const float* Y, float slope, int j, float u, int B) {
+    float f = __fadd_rn(Y[j], __fmul_rn(__fsub_rn(u, X[j]), slope));
+    f = f < Y[j] ? Y[j] : f;
+    f = f > Y[j + 1] ? Y[j + 1] : f;
+    const uint32_t b = (uint32_t)__fmul_rn(f, __int2float_rn(B));
+    return b > (uint32_t)(B - 1) ? (uint32_t)(B - 1) : b;
+}
+
+__device__ __forceinline__ uint32_t pwl_bucket(const float* X, const float* Y, float u, int B) {
+    const int j = u < X[kPwlSegments] ? pwl_segment(X, u) : kPwlSegments - 1;
+    return pwl_bucket_in(X, Y, pwl_slope(X, Y, j), j, u, B);
 }
 
 }  // namespace isort

@@ -152,23 +152,30 @@ def test_splitters_bit_exact(cuda_lib, width, kb, B):
     assert np.array_equal(got, exp)
 
 
-@pytest.mark.parametrize("width,B", [(32, 4096), (32, 16384), (64, 4096), (32, 3)])
-def test_bucket_ids_bit_exact(cuda_lib, width, B):
+@pytest.mark.parametrize("width,kb,B", [(32, 32, 4096), (32, 32, 16384), (32, 20, 1000), (64, 64, 4096),
+                                        (32, 32, 3), (32, 32, 65536)])
+def test_bucket_ids_bit_exact(cuda_lib, width, kb, B):
     import torch
 
-    X, Y = _test_knots(100 + B)
-    split = oracle.splitters(X, Y, width, width, B)
+    X, Y = _test_knots(100 + B + kb)
+    split = oracle.splitters(X, Y, width, kb, B)
     n = 1_000_003
     if width == 32:
-        keys = gen.uniform_u32(n, 32, 10, 0)
-        keys[:1000] = split[B // 2].astype(np.uint32)  # keys equal to a splitter
-        dsplit = to_dev(split.astype(np.uint32))
+        keys = gen.uniform_u32(n, kb, 10, 0)
+        keys[:1000] = split[B // 2].astype(np.uint32)  # the first keys of buckets and their predecessors
+        keys[1000:2000] = (np.maximum(split[B // 2], 1) - 1).astype(np.uint32)
     else:
         keys = gen.uniform_u64(n, 64, 10, 0)
         keys[:1000] = split[B // 2]
-        dsplit = to_dev(split)
-    ids = cuda_lib.bucket_ids(to_dev(keys), torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), dsplit)
-    assert np.array_equal(to_np(ids, np.uint32), oracle.bucket_ids(keys, split))
+        keys[1000:2000] = np.maximum(split[B // 2], 1) - 1
+    ids = cuda_lib.bucket_ids(to_dev(keys), torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), B, kb)
+    got = to_np(ids, np.uint32)
+    assert np.array_equal(got, oracle.bucket_ids(keys, X, Y, kb, B))
+    # and the GPU's own splitter table bounds the GPU's buckets
+    s = cuda_lib.cdf_splitters(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), key_width=width, key_bits=kb,
+                               nbuckets=B)
+    gs = to_np(s, np.uint32 if width == 32 else np.uint64).astype(np.uint64)
+    assert np.array_equal(got, np.searchsorted(gs[1:], keys.astype(np.uint64), side="right").astype(np.uint32))
 
 
 def test_training_reduces_loss_and_reports_it(cuda_lib):
