@@ -37,7 +37,7 @@ struct Tune {
     int shape_small = 4;  // launch shape for digits of <= 8 bits
     int shape_large = 1;  // launch shape for wider digits
     int algo = 1;         // 0: single-pass rounds with look-back, 1: chunked reduce-then-scan rounds
-    int sweep_small = 3;  // chunked-round launch shape, digits of <= 8 bits
+    int sweep_small = 4;  // chunked-round launch shape, digits of <= 8 bits (4: half-warp ranking)
     int sweep_large = 2;  // chunked-round launch shape, wider digits
 };
 
@@ -61,7 +61,7 @@ static Tune load_tune() {
         p += used;
         if (*p == ',') ++p;
     }
-    if (t.sweep_small < 0 || t.sweep_small >= 4) t.sweep_small = 3;
+    if (t.sweep_small < 0 || t.sweep_small >= 5) t.sweep_small = 3;
     if (t.sweep_large < 0 || t.sweep_large >= 4) t.sweep_large = 2;
     if (t.shape_small < 0 || t.shape_small >= 13) t.shape_small = 4;
     if (t.shape_large < 0 || t.shape_large >= 13) t.shape_large = 1;
@@ -825,8 +825,10 @@ isort_status launch_round_dispatch(int sh, bool vals, PassArgs a, cudaStream_t s
 }
 
 // ---- chunked reduce-then-scan rounds
-constexpr int kSweepThreads[] = {256, 512, 256, 512};
-constexpr int kSweepItems[] = {16, 16, 8, 8};
+// shapes 0-3: the generic chunked round; 4: the half-warp ranking variant
+// (8-bit digits only; 512 x 8)
+constexpr int kSweepThreads[] = {256, 512, 256, 512, 512};
+constexpr int kSweepItems[] = {16, 16, 8, 8, 8};
 
 int sweep_tile(int sh) { return kSweepThreads[sh] * kSweepItems[sh]; }
 
@@ -861,6 +863,22 @@ isort_status launch_sweep(const SweepArgs& a, uint32_t chunks, cudaStream_t s) {
 }
 
 template <typename K, bool VALS>
+isort_status sweep_occupancy_hw(int* per_sm) {
+    const size_t smem = HwCfg<K, VALS>::smem_bytes();
+    if (smem > max_smem_optin()) return ISORT_ERR_UNSUPPORTED;
+    ISORT_TRY_CUDA(cudaFuncSetAttribute(k_downsweep_hw<K, VALS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ISORT_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_downsweep_hw<K, VALS>, kHwThreads, smem));
+    return *per_sm >= 1 ? ISORT_OK : ISORT_ERR_UNSUPPORTED;
+}
+
+template <typename K, bool VALS>
+isort_status launch_sweep_hw(const SweepArgs& a, uint32_t chunks, cudaStream_t s) {
+    LaunchScope ls("downsweep", s);
+    k_downsweep_hw<K, VALS><<<chunks, kHwThreads, HwCfg<K, VALS>::smem_bytes(), s>>>(a);
+    return from_cuda(cudaGetLastError());
+}
+
+template <typename K, bool VALS>
 isort_status sweep_dispatch(int sh, bool occupancy_only, int bins, int* per_sm, const SweepArgs* a, uint32_t chunks,
                             cudaStream_t s) {
     switch (sh) {
@@ -873,6 +891,17 @@ isort_status sweep_dispatch(int sh, bool occupancy_only, int bins, int* per_sm, 
         case 2:
             return occupancy_only ? sweep_occupancy<K, VALS, 256, 8>(bins, per_sm)
                                   : launch_sweep<K, VALS, 256, 8>(*a, chunks, s);
+        case 4:
+            if (bins == kHwBins) {
+                if (occupancy_only) return sweep_occupancy_hw<K, VALS>(per_sm);
+                return launch_sweep_hw<K, VALS>(*a, chunks, s);
+            }
+            if (!occupancy_only) {  // a narrower final digit: the generic 512 x 8 round (same tile)
+                int tmp = 0;
+                const isort_status so = sweep_occupancy<K, VALS, 512, 8>(bins, &tmp);
+                if (so != ISORT_OK) return so;
+            }
+            [[fallthrough]];
         default:
             return occupancy_only ? sweep_occupancy<K, VALS, 512, 8>(bins, per_sm)
                                   : launch_sweep<K, VALS, 512, 8>(*a, chunks, s);

@@ -417,3 +417,217 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
 }
 
 }  // namespace isort
+
+namespace isort {
+
+// ---------------------------------------------------------------- half-warp ranking
+//
+// A variant of the chunked round for 8-bit digits (512 threads, 8 keys per
+// thread) whose ranking state is ONE 32-bit word per (half-warp, digit): bits
+// [16, 32) count the digit's keys the half-warp has seen, bits [0, 16) collect
+// the lanes holding the digit in the current item. A key costs one atomicAdd,
+// one read and (for the group's highest lane) one write, against five
+// accesses with separate count and peer-mask arrays; after ranking the same
+// words hold each (half-warp, digit)'s output base, so staging reads one word.
+// Each half-warp owns 128 consecutive keys of the tile (8 items of 16 keys);
+// blocks sit 144 elements apart in shared memory so that the two half-warps of
+// a warp read disjoint banks.
+constexpr int kHwThreads = 512;
+constexpr int kHwItems = 8;
+constexpr int kHwTile = kHwThreads * kHwItems;  // 4096 keys
+constexpr int kHwGroups = kHwThreads / 16;       // 32 half-warps
+constexpr int kHwBlock = 16 * kHwItems;          // 128 keys per half-warp
+constexpr int kHwPitch = kHwBlock + 16;          // block pitch in shared memory (elements)
+constexpr int kHwBins = 256;
+
+template <typename K, bool VALS>
+struct HwCfg {
+    static constexpr size_t kKeyBytes = (size_t)kHwGroups * kHwPitch * sizeof(K);
+    static constexpr size_t kValBytes = VALS ? (size_t)kHwGroups * kHwPitch * 4 : 0;
+    static constexpr size_t kBufBytes = kKeyBytes + kValBytes;
+    static size_t smem_bytes() {
+        return 2 * kBufBytes + (size_t)kHwGroups * kHwBins * 4  // buffers, ranking words
+               + (size_t)kHwBins * 4 * 6                       // start, tot, run, delta, half totals (2)
+               + 2 * 8 + 32 * 4 + 16;                          // mbarriers, scan scratch
+    }
+};
+
+template <typename K, bool VALS, bool FULL>
+__device__ __forceinline__ void hw_tile(const SweepArgs& a, K* s_keys, uint32_t* s_vals, uint32_t* s_word,
+                                       uint32_t* s_start, uint32_t* s_tot, uint32_t* s_run, uint32_t* s_delta,
+                                       uint32_t* s_half, uint32_t* s_warp_scan, uint32_t tile_n) {
+    const int tid = threadIdx.x, lane = tid & 31, hw = tid >> 4, l16 = lane & 15;
+    const int shift = a.shift;
+    uint32_t* my_w = s_word + hw * kHwBins;
+    const uint32_t bit = 1u << l16, lt16 = bit - 1u;
+    K kreg[kHwItems];
+    uint32_t vreg[kHwItems];
+    uint32_t rank[kHwItems];
+    uint32_t dreg[kHwItems];
+#pragma unroll
+    for (int i = 0; i < kHwItems; ++i) {
+        const uint32_t j = (uint32_t)(hw * kHwBlock + i * 16 + l16);  // position in the tile (input order)
+        const bool valid = FULL || j < tile_n;
+        const int p = hw * kHwPitch + i * 16 + l16;
+        const K k = valid ? s_keys[p] : (K)0;
+        kreg[i] = k;
+        if constexpr (VALS) vreg[i] = valid ? s_vals[p] : 0u;
+        const uint32_t d = valid ? (uint32_t)(k >> shift) & (kHwBins - 1) : 0u;
+        if (valid) atomicAdd(&my_w[d], 0x10000u | bit);
+        __syncwarp();
+        const uint32_t x = valid ? my_w[d] : 0u;
+        const uint32_t m = x & 0xFFFFu;
+        rank[i] = (x >> 16) - (uint32_t)__popc(m) + (uint32_t)__popc(m & lt16);
+        dreg[i] = d;
+        __syncwarp();
+        if (valid && (m >> l16) == 1u) my_w[d] = x & 0xFFFF0000u;  // the group's highest lane clears the lanes
+        __syncwarp();
+    }
+    __syncthreads();
+    {  // per digit: counts -> exclusive prefixes over half-warps, in two halves of 16
+        const int half = tid >> 8, d = tid & (kHwBins - 1);
+        uint32_t sum = 0;
+#pragma unroll 4
+        for (int h = half * 16; h < half * 16 + 16; ++h) {
+            const uint32_t c = s_word[h * kHwBins + d] >> 16;
+            s_word[h * kHwBins + d] = sum;
+            sum += c;
+        }
+        s_half[half * kHwBins + d] = sum;
+    }
+    __syncthreads();
+    if (tid < kHwBins) {
+        const uint32_t t = s_half[tid] + s_half[kHwBins + tid];
+        s_tot[tid] = t;
+        s_start[tid] = t;
+    }
+    __syncthreads();
+    block_exclusive_scan<kHwThreads>(s_start, kHwBins, s_warp_scan);
+    {  // bases of every (half-warp, digit); the round's output offsets
+        const int half = tid >> 8, d = tid & (kHwBins - 1);
+        const uint32_t add = s_start[d] + (half ? s_half[d] : 0u);
+#pragma unroll 4
+        for (int h = half * 16; h < half * 16 + 16; ++h) s_word[h * kHwBins + d] += add;
+        if (tid < kHwBins) s_delta[tid] = s_run[tid] - s_start[tid];
+    }
+    __syncthreads();
+    // stage by digit (linear, over the tile's own buffer: its keys are in registers)
+#pragma unroll
+    for (int i = 0; i < kHwItems; ++i) {
+        const uint32_t j = (uint32_t)(hw * kHwBlock + i * 16 + l16);
+        if (FULL || j < tile_n) {
+            const uint32_t pos = my_w[dreg[i]] + rank[i];
+            if (pos < (uint32_t)kHwTile) {
+                s_keys[pos] = kreg[i];
+                if constexpr (VALS) s_vals[pos] = vreg[i];
+            }
+        }
+    }
+    __syncthreads();
+    K* keys_out = static_cast<K*>(a.keys_out);
+#pragma unroll
+    for (int i = 0; i < kHwItems; ++i) {
+        const uint32_t j = (uint32_t)(tid + i * kHwThreads);
+        if (FULL || j < tile_n) {
+            const K k = s_keys[j];
+            const uint32_t d = (uint32_t)(k >> shift) & (kHwBins - 1);
+            const uint32_t dst = s_delta[d] + j;
+            if (dst < a.n) {
+                keys_out[dst] = k;
+                if constexpr (VALS) a.vals_out[dst] = s_vals[j];
+            } else {
+                set_status(a.status, kStatBounds);
+            }
+        }
+    }
+    {  // clear the ranking words for the next tile (16-byte stores)
+        uint4* w4 = reinterpret_cast<uint4*>(s_word);
+        for (int i = tid; i < kHwGroups * kHwBins / 4; i += kHwThreads) w4[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (tid < kHwBins) s_run[tid] += s_tot[tid];
+    __syncthreads();
+}
+
+template <typename K, bool VALS>
+__global__ void __launch_bounds__(kHwThreads, 2) k_downsweep_hw(SweepArgs a) {
+    using Cfg = HwCfg<K, VALS>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned char* buf0 = smem;
+    uint32_t* s_word = reinterpret_cast<uint32_t*>(smem + 2 * Cfg::kBufBytes);
+    uint32_t* s_start = s_word + kHwGroups * kHwBins;
+    uint32_t* s_tot = s_start + kHwBins;
+    uint32_t* s_run = s_tot + kHwBins;
+    uint32_t* s_delta = s_run + kHwBins;
+    uint32_t* s_half = s_delta + kHwBins;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(s_half + 2 * kHwBins);
+    uint32_t* s_warp_scan = reinterpret_cast<uint32_t*>(bars + 2);
+    if ((size_t)(reinterpret_cast<unsigned char*>(s_warp_scan + 32) - smem) > dynamic_smem_size()) {
+        if (tid == 0) set_status(a.status, kStatBounds);
+        return;
+    }
+    if (__syncthreads_or(tid == 0 && *(volatile uint32_t*)a.status != 0)) return;
+    const uint32_t t_begin = blockIdx.x * a.chunk_tiles;
+    const uint32_t t_end = min(a.num_tiles, t_begin + a.chunk_tiles);
+    if (t_begin >= t_end) return;
+    const K* keys_in = static_cast<const K*>(a.keys_in);
+
+    for (int i = tid; i < kHwGroups * kHwBins; i += kHwThreads) s_word[i] = 0u;
+    for (int d = tid; d < kHwBins; d += kHwThreads) s_run[d] = a.chunk_off[(size_t)blockIdx.x * kHwBins + d];
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    auto full_bulk_tile = [&](uint32_t t) -> bool { return a.use_bulk && (size_t)(t + 1) * kHwTile <= a.n; };
+    // warp 0: lane 0 announces the bytes, then lane l copies half-warp block l
+    auto issue_tile = [&](uint32_t t, int b) {
+        unsigned char* dst = buf0 + (size_t)b * Cfg::kBufBytes;
+        constexpr uint32_t kb = kHwBlock * sizeof(K);
+        if (lane == 0) mbar_arrive_expect_tx(&bars[b], kHwTile * (uint32_t)sizeof(K) + (VALS ? kHwTile * 4u : 0u));
+        __syncwarp();
+        fence_proxy_async_smem();
+        bulk_load(dst + (size_t)lane * kHwPitch * sizeof(K), keys_in + (size_t)t * kHwTile + (size_t)lane * kHwBlock, kb,
+                  &bars[b]);
+        if constexpr (VALS)
+            bulk_load(dst + Cfg::kKeyBytes + (size_t)lane * kHwPitch * 4,
+                      a.vals_in + (size_t)t * kHwTile + (size_t)lane * kHwBlock, kHwBlock * 4, &bars[b]);
+    };
+    if (warp == 0 && full_bulk_tile(t_begin)) issue_tile(t_begin, 0);
+    uint32_t phase = 0u;
+    int b = 0;
+    for (uint32_t tile = t_begin; tile < t_end; ++tile, b ^= 1) {
+        if (warp == 0 && tile + 1 < t_end && full_bulk_tile(tile + 1)) issue_tile(tile + 1, b ^ 1);
+        K* s_keys = reinterpret_cast<K*>(buf0 + (size_t)b * Cfg::kBufBytes);
+        uint32_t* s_vals = reinterpret_cast<uint32_t*>(buf0 + (size_t)b * Cfg::kBufBytes + Cfg::kKeyBytes);
+        const uint32_t tile_base = tile * (uint32_t)kHwTile;
+        const uint32_t tile_n = min((uint32_t)kHwTile, a.n - tile_base);
+        bool ok = true;
+        if (full_bulk_tile(tile)) {
+            ok = mbar_wait_bounded(&bars[b], (phase >> b) & 1u, a.limit_ns);
+            phase ^= 1u << b;
+        } else {
+            for (uint32_t j = tid; j < tile_n; j += kHwThreads) {
+                const uint32_t p = (j / kHwBlock) * kHwPitch + (j % kHwBlock);
+                s_keys[p] = keys_in[tile_base + j];
+                if constexpr (VALS) s_vals[p] = a.vals_in[tile_base + j];
+            }
+        }
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) set_status(a.status, kStatTimeout);
+            if (tile + 1 < t_end && full_bulk_tile(tile + 1))
+                mbar_wait_bounded(&bars[b ^ 1], (phase >> (b ^ 1)) & 1u, a.limit_ns);
+            return;
+        }
+        if (tile_n == (uint32_t)kHwTile)
+            hw_tile<K, VALS, true>(a, s_keys, s_vals, s_word, s_start, s_tot, s_run, s_delta, s_half, s_warp_scan,
+                                   kHwTile);
+        else
+            hw_tile<K, VALS, false>(a, s_keys, s_vals, s_word, s_start, s_tot, s_run, s_delta, s_half, s_warp_scan,
+                                    tile_n);
+    }
+}
+
+}  // namespace isort
