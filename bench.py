@@ -240,14 +240,20 @@ def run_ours(args):
     rl, rms = prof.get(round_kernel, (0, 0.0))
     avg_round_ms = rms / max(rl, 1)
     achieved = N * ROUND_BYTES_PER_KEY / (avg_round_ms * 1e-3) / 1e9 if rl else None
+    # DRAM bytes per launch of that kernel from one ncu capture (a "key: value"
+    # text summary under profiles/), when it was taken on this workload
     traffic = None
-    tpath = os.path.join(ROOT, "profiles", f"{round_kernel}_traffic.json")
+    tpath = os.path.join(ROOT, "profiles", f"{round_kernel}_traffic.txt")
     if os.path.exists(tpath):
         try:
+            t = {}
             with open(tpath) as f:
-                t = json.load(f)
-            if t.get("log2n") == int(round(np.log2(N))) and t.get("radix_bits") == RADIX_BITS:
-                traffic = t.get("bytes_per_launch")
+                for ln in f:
+                    if ":" in ln and not ln.startswith("#"):
+                        k, v = ln.split(":", 1)
+                        t[k.strip()] = v.strip()
+            if int(t.get("log2n", -1)) == int(round(np.log2(N))) and int(t.get("radix_bits", -1)) == RADIX_BITS:
+                traffic = float(t["bytes_per_launch"])
         except Exception:
             traffic = None
     kernels = {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in prof.items()}

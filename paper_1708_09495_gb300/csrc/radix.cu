@@ -826,7 +826,7 @@ isort_status launch_round_dispatch(int sh, bool vals, PassArgs a, cudaStream_t s
 
 // ---- chunked reduce-then-scan rounds
 // shapes 0-3: the generic chunked round; 4: the half-warp ranking variant
-// (8-bit digits only; 512 x 8)
+// (u32 keys and 8-bit digits; 512 x 8; other cases take shape 3)
 constexpr int kSweepThreads[] = {256, 512, 256, 512, 512};
 constexpr int kSweepItems[] = {16, 16, 8, 8, 8};
 
@@ -892,11 +892,12 @@ isort_status sweep_dispatch(int sh, bool occupancy_only, int bins, int* per_sm, 
             return occupancy_only ? sweep_occupancy<K, VALS, 256, 8>(bins, per_sm)
                                   : launch_sweep<K, VALS, 256, 8>(*a, chunks, s);
         case 4:
-            if (bins == kHwBins) {
+            // u32 keys only: with u64 keys its padded buffers leave one CTA per SM
+            if (bins == kHwBins && sizeof(K) == 4) {
                 if (occupancy_only) return sweep_occupancy_hw<K, VALS>(per_sm);
                 return launch_sweep_hw<K, VALS>(*a, chunks, s);
             }
-            if (!occupancy_only) {  // a narrower final digit: the generic 512 x 8 round (same tile)
+            if (!occupancy_only) {  // otherwise the generic 512 x 8 round (same tile)
                 int tmp = 0;
                 const isort_status so = sweep_occupancy<K, VALS, 512, 8>(bins, &tmp);
                 if (so != ISORT_OK) return so;
