@@ -100,6 +100,21 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The largest per-rank time (replicas: the job ends when the slowest rank does)."""
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world: int, steps: int, n: int, ms_max: float) -> float:
+    """Whole-job throughput in Gkeys/s: every rank sorts n keys per step."""
+    return world * steps * n / (ms_max * 1e-3) / 1e9
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -226,11 +241,8 @@ def run_ours(args):
     launches = isort.launch_count() - launches0
     ms = e0.elapsed_time(e1)
     prof = isort.profile_read()
-    ms_t = torch.tensor([ms], device="cuda")
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = world * args.steps * N / (ms_max * 1e-3) / 1e9
+    ms_max = max_over_ranks(ms, dist, "cuda")
+    value = replica_value(world, args.steps, N, ms_max)
 
     # dominant kernel: the rank-and-scatter launch of a round (chunked rounds:
     # "downsweep"; single-pass rounds: "onesweep"). Algorithmic bytes per
