@@ -366,7 +366,59 @@ def run_compare(args):
     peak, peak_kind = peaks()
     line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "dtype": "u32", "data": "synthetic"}
-    if args.workload == "learned":
+    if args.workload == "small":
+        # the small case: LSD on 65,536 keys (keys only, radix 2^8), BTN and OET
+        # on its first 1,024 keys; launch-bound, reported in microseconds per call
+        keys = workloads.small_uniform()
+        n = keys.size
+        kin = torch.from_numpy(keys.view(np.int32)).cuda()
+        kout = torch.empty_like(kin)
+        small = torch.from_numpy(keys[: workloads.SMALL_BTN_N].copy().view(np.int32)).cuda()
+        sw = torch.empty_like(small)
+        iters = max(50, args.steps)
+
+        def timed(call, reset=None):
+            for _ in range(args.warmup):
+                if reset:
+                    reset()
+                call()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            tot = 0.0
+            for _ in range(iters):
+                if reset:
+                    reset()
+                e0.record(stream)
+                call()
+                e1.record(stream)
+                e1.synchronize()
+                tot += e0.elapsed_time(e1)
+            return tot / iters * 1e3  # microseconds per call
+
+        def lsd():
+            rc = lib.isort_radix_copy(ctypes.c_void_p(kin.data_ptr()), None, ctypes.c_void_p(kout.data_ptr()), None,
+                                      n, 32, 8, sp)
+            if rc != 0:
+                raise RuntimeError(f"isort_radix_copy: {isort.STATUS.get(rc, rc)}")
+
+        def net(fn):
+            def call():
+                rc = fn(ctypes.c_void_p(sw.data_ptr()), None, sw.numel(), sp)
+                if rc != 0:
+                    raise RuntimeError(f"network sort: {isort.STATUS.get(rc, rc)}")
+            return call
+
+        us_lsd = timed(lsd)
+        us_btn = timed(net(lib.isort_btn), lambda: sw.copy_(small))
+        us_oet = timed(net(lib.isort_oet), lambda: sw.copy_(small))
+        line.update({
+            "value": n / (us_lsd * 1e-6) / 1e9, "ms_per_step": us_lsd * 1e-3,
+            "config": {"workload": "65,536 u32 keys uniform (seed 1), keys only, radix 2^8, out of place; "
+                                   "BTN and OET on the first 1,024 keys", "iters": iters},
+            "us_per_call": {"lsd_65536": us_lsd, "btn_1024": us_btn, "oet_1024": us_oet},
+            "note": "launch-bound sizes: microseconds per call, not a roofline",
+        })
+    elif args.workload == "learned":
         n = 1 << args.log2n
         keys = workloads.skewed(args.dist, n)
         kin = torch.from_numpy(keys.view(np.int32)).cuda()
@@ -475,8 +527,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--log2n", type=int, default=28)
     ap.add_argument("--radix-bits", type=int, default=8)
-    ap.add_argument("--workload", default="uniform", choices=["uniform", "learned", "segmented"],
-                    help="uniform: the benchmark; learned / segmented: secondary comparisons with plain LSD")
+    ap.add_argument("--workload", default="uniform", choices=["uniform", "learned", "segmented", "small"],
+                    help="uniform: the benchmark; learned / segmented: secondary comparisons with plain LSD; "
+                         "small: the 65,536-key case and the block networks on 1,024 keys")
     ap.add_argument("--dist", default="lognormal", choices=["zipf", "lognormal", "gmm"])
     args = ap.parse_args()
     configure(args)

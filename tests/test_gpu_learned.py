@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import gen
+import gen.workloads
 import oracle
 from tests._util import to_dev, to_np
 
@@ -55,6 +56,21 @@ def test_learned_matches_oracle(cuda_lib, kind):
     if kind == "uniform":
         assert not st["fell_back_to_lsd"]
         assert st["imbalance_max_over_mean"] < 2.0
+
+
+@pytest.mark.parametrize("kind", ["lognormal", "zipf"])
+def test_learned_full_size_keys_only(cuda_lib, kind):
+    """The benchmark's learned workload: 2^28 skewed u32 keys, keys only,
+    bucket count chosen by the library, against the oracle's sort."""
+    keys = gen.workloads.skewed(kind, 1 << 28)
+    dk = to_dev(keys)
+    st = cuda_lib.learned(dk, None)
+    got = to_np(dk, np.uint32)
+    del dk
+    ek, _ = oracle.lsd(keys, None, 0, 8)
+    assert np.array_equal(got, ek)
+    if kind == "lognormal":
+        assert st["nbuckets"] == 16384 and not st["fell_back_to_lsd"]
 
 
 def test_learned_keys_only_and_key_bits(cuda_lib):
