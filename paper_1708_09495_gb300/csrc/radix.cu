@@ -61,7 +61,7 @@ static Tune load_tune() {
         p += used;
         if (*p == ',') ++p;
     }
-    if (t.sweep_small < 0 || t.sweep_small >= 5) t.sweep_small = 3;
+    if (t.sweep_small < 0 || t.sweep_small >= 7) t.sweep_small = 4;
     if (t.sweep_large < 0 || t.sweep_large >= 4) t.sweep_large = 2;
     if (t.shape_small < 0 || t.shape_small >= 13) t.shape_small = 4;
     if (t.shape_large < 0 || t.shape_large >= 13) t.shape_large = 1;
@@ -825,10 +825,10 @@ isort_status launch_round_dispatch(int sh, bool vals, PassArgs a, cudaStream_t s
 }
 
 // ---- chunked reduce-then-scan rounds
-// shapes 0-3: the generic chunked round; 4: the half-warp ranking variant
-// (u32 keys and 8-bit digits; 512 x 8; other cases take shape 3)
-constexpr int kSweepThreads[] = {256, 512, 256, 512, 512};
-constexpr int kSweepItems[] = {16, 16, 8, 8, 8};
+// shapes 0-3: the generic chunked round; 4-6: the half-warp ranking variant
+// (u32 keys and 8-bit digits; other cases take the generic round of the same tile)
+constexpr int kSweepThreads[] = {256, 512, 256, 512, 512, 256, 512};
+constexpr int kSweepItems[] = {16, 16, 8, 8, 8, 16, 16};
 
 int sweep_tile(int sh) { return kSweepThreads[sh] * kSweepItems[sh]; }
 
@@ -862,20 +862,39 @@ isort_status launch_sweep(const SweepArgs& a, uint32_t chunks, cudaStream_t s) {
     return from_cuda(cudaGetLastError());
 }
 
-template <typename K, bool VALS>
+template <typename K, bool VALS, int THREADS, int ITEMS>
 isort_status sweep_occupancy_hw(int* per_sm) {
-    const size_t smem = HwCfg<K, VALS>::smem_bytes();
+    const size_t smem = HwCfg<K, VALS, THREADS, ITEMS>::smem_bytes();
     if (smem > max_smem_optin()) return ISORT_ERR_UNSUPPORTED;
-    ISORT_TRY_CUDA(cudaFuncSetAttribute(k_downsweep_hw<K, VALS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    ISORT_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_downsweep_hw<K, VALS>, kHwThreads, smem));
+    auto kern = k_downsweep_hw<K, VALS, THREADS, ITEMS>;
+    ISORT_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ISORT_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, THREADS, smem));
     return *per_sm >= 1 ? ISORT_OK : ISORT_ERR_UNSUPPORTED;
 }
 
-template <typename K, bool VALS>
+template <typename K, bool VALS, int THREADS, int ITEMS>
 isort_status launch_sweep_hw(const SweepArgs& a, uint32_t chunks, cudaStream_t s) {
     LaunchScope ls("downsweep", s);
-    k_downsweep_hw<K, VALS><<<chunks, kHwThreads, HwCfg<K, VALS>::smem_bytes(), s>>>(a);
+    k_downsweep_hw<K, VALS, THREADS, ITEMS><<<chunks, THREADS, HwCfg<K, VALS, THREADS, ITEMS>::smem_bytes(), s>>>(a);
     return from_cuda(cudaGetLastError());
+}
+
+// The half-warp round for u32 keys and 8-bit digits; other cases take the
+// generic round of the same tile.
+template <typename K, bool VALS, int THREADS, int ITEMS>
+isort_status sweep_hw_or_generic(bool occupancy_only, int bins, int* per_sm, const SweepArgs* a, uint32_t chunks,
+                                 cudaStream_t s) {
+    if constexpr (sizeof(K) == 4) {  // with u64 keys the padded buffers leave one CTA per SM
+        if (bins == kHwBins) {
+            if (occupancy_only) return sweep_occupancy_hw<K, VALS, THREADS, ITEMS>(per_sm);
+            return launch_sweep_hw<K, VALS, THREADS, ITEMS>(*a, chunks, s);
+        }
+    }
+    if (occupancy_only) return sweep_occupancy<K, VALS, THREADS, ITEMS>(bins, per_sm);
+    int tmp = 0;
+    const isort_status so = sweep_occupancy<K, VALS, THREADS, ITEMS>(bins, &tmp);  // sets the kernel's attribute
+    if (so != ISORT_OK) return so;
+    return launch_sweep<K, VALS, THREADS, ITEMS>(*a, chunks, s);
 }
 
 template <typename K, bool VALS>
@@ -892,17 +911,11 @@ isort_status sweep_dispatch(int sh, bool occupancy_only, int bins, int* per_sm, 
             return occupancy_only ? sweep_occupancy<K, VALS, 256, 8>(bins, per_sm)
                                   : launch_sweep<K, VALS, 256, 8>(*a, chunks, s);
         case 4:
-            // u32 keys only: with u64 keys its padded buffers leave one CTA per SM
-            if (bins == kHwBins && sizeof(K) == 4) {
-                if (occupancy_only) return sweep_occupancy_hw<K, VALS>(per_sm);
-                return launch_sweep_hw<K, VALS>(*a, chunks, s);
-            }
-            if (!occupancy_only) {  // otherwise the generic 512 x 8 round (same tile)
-                int tmp = 0;
-                const isort_status so = sweep_occupancy<K, VALS, 512, 8>(bins, &tmp);
-                if (so != ISORT_OK) return so;
-            }
-            [[fallthrough]];
+            return sweep_hw_or_generic<K, VALS, 512, 8>(occupancy_only, bins, per_sm, a, chunks, s);
+        case 5:
+            return sweep_hw_or_generic<K, VALS, 256, 16>(occupancy_only, bins, per_sm, a, chunks, s);
+        case 6:
+            return sweep_hw_or_generic<K, VALS, 512, 16>(occupancy_only, bins, per_sm, a, chunks, s);
         default:
             return occupancy_only ? sweep_occupancy<K, VALS, 512, 8>(bins, per_sm)
                                   : launch_sweep<K, VALS, 512, 8>(*a, chunks, s);

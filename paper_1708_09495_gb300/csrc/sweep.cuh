@@ -432,43 +432,51 @@ namespace isort {
 // Each half-warp owns 128 consecutive keys of the tile (8 items of 16 keys);
 // blocks sit 144 elements apart in shared memory so that the two half-warps of
 // a warp read disjoint banks.
-constexpr int kHwThreads = 512;
-constexpr int kHwItems = 8;
-constexpr int kHwTile = kHwThreads * kHwItems;  // 4096 keys
-constexpr int kHwGroups = kHwThreads / 16;       // 32 half-warps
-constexpr int kHwBlock = 16 * kHwItems;          // 128 keys per half-warp
-constexpr int kHwPitch = kHwBlock + 16;          // block pitch in shared memory (elements)
 constexpr int kHwBins = 256;
 
-template <typename K, bool VALS>
+// THREADS x ITEMS keys per tile; THREADS / 16 half-warps each own 16 x ITEMS
+// consecutive keys (ITEMS even, so that the 16-element pitch shift puts the
+// two half-warps of a warp on disjoint banks); counts per half-warp and digit
+// stay below 2^16.
+template <typename K, bool VALS, int THREADS, int ITEMS>
 struct HwCfg {
-    static constexpr size_t kKeyBytes = (size_t)kHwGroups * kHwPitch * sizeof(K);
-    static constexpr size_t kValBytes = VALS ? (size_t)kHwGroups * kHwPitch * 4 : 0;
+    static_assert(THREADS == 256 || THREADS == 512, "one or two threads per digit");
+    static_assert(ITEMS % 2 == 0 && 16 * ITEMS < 65536, "pitch and count width");
+    static constexpr int kTile = THREADS * ITEMS;
+    static constexpr int kGroups = THREADS / 16;
+    static constexpr int kBlock = 16 * ITEMS;
+    static constexpr int kPitch = kBlock + 16;
+    static constexpr int kHalves = THREADS / kHwBins;  // threads per digit in the per-digit steps
+    static constexpr size_t kKeyBytes = (size_t)kGroups * kPitch * sizeof(K);
+    static constexpr size_t kValBytes = VALS ? (size_t)kGroups * kPitch * 4 : 0;
     static constexpr size_t kBufBytes = kKeyBytes + kValBytes;
     static size_t smem_bytes() {
-        return 2 * kBufBytes + (size_t)kHwGroups * kHwBins * 4  // buffers, ranking words
-               + (size_t)kHwBins * 4 * 6                       // start, tot, run, delta, half totals (2)
-               + 2 * 8 + 32 * 4 + 16;                          // mbarriers, scan scratch
+        return 2 * kBufBytes + (size_t)kGroups * kHwBins * 4  // buffers, ranking words
+               + (size_t)kHwBins * 4 * 6                     // start, tot, run, delta, half totals (2)
+               + 2 * 8 + 32 * 4 + 16;                        // mbarriers, scan scratch
     }
 };
 
-template <typename K, bool VALS, bool FULL>
+template <typename K, bool VALS, int THREADS, int ITEMS, bool FULL>
 __device__ __forceinline__ void hw_tile(const SweepArgs& a, K* s_keys, uint32_t* s_vals, uint32_t* s_word,
                                        uint32_t* s_start, uint32_t* s_tot, uint32_t* s_run, uint32_t* s_delta,
                                        uint32_t* s_half, uint32_t* s_warp_scan, uint32_t tile_n) {
+    using Cfg = HwCfg<K, VALS, THREADS, ITEMS>;
+    constexpr int kTile = Cfg::kTile, kBlock = Cfg::kBlock, kPitch = Cfg::kPitch, kGroups = Cfg::kGroups;
+    constexpr int kPerHalf = kGroups / Cfg::kHalves;
     const int tid = threadIdx.x, lane = tid & 31, hw = tid >> 4, l16 = lane & 15;
     const int shift = a.shift;
     uint32_t* my_w = s_word + hw * kHwBins;
     const uint32_t bit = 1u << l16, lt16 = bit - 1u;
-    K kreg[kHwItems];
-    uint32_t vreg[kHwItems];
-    uint32_t rank[kHwItems];
-    uint32_t dreg[kHwItems];
+    K kreg[ITEMS];
+    uint32_t vreg[ITEMS];
+    uint32_t rank[ITEMS];
+    uint32_t dreg[ITEMS];
 #pragma unroll
-    for (int i = 0; i < kHwItems; ++i) {
-        const uint32_t j = (uint32_t)(hw * kHwBlock + i * 16 + l16);  // position in the tile (input order)
+    for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t j = (uint32_t)(hw * kBlock + i * 16 + l16);  // position in the tile (input order)
         const bool valid = FULL || j < tile_n;
-        const int p = hw * kHwPitch + i * 16 + l16;
+        const int p = hw * kPitch + i * 16 + l16;
         const K k = valid ? s_keys[p] : (K)0;
         kreg[i] = k;
         if constexpr (VALS) vreg[i] = valid ? s_vals[p] : 0u;
@@ -488,7 +496,7 @@ __device__ __forceinline__ void hw_tile(const SweepArgs& a, K* s_keys, uint32_t*
         const int half = tid >> 8, d = tid & (kHwBins - 1);
         uint32_t sum = 0;
 #pragma unroll 4
-        for (int h = half * 16; h < half * 16 + 16; ++h) {
+        for (int h = half * kPerHalf; h < half * kPerHalf + kPerHalf; ++h) {
             const uint32_t c = s_word[h * kHwBins + d] >> 16;
             s_word[h * kHwBins + d] = sum;
             sum += c;
@@ -497,27 +505,27 @@ __device__ __forceinline__ void hw_tile(const SweepArgs& a, K* s_keys, uint32_t*
     }
     __syncthreads();
     if (tid < kHwBins) {
-        const uint32_t t = s_half[tid] + s_half[kHwBins + tid];
+        const uint32_t t = Cfg::kHalves == 2 ? s_half[tid] + s_half[kHwBins + tid] : s_half[tid];
         s_tot[tid] = t;
         s_start[tid] = t;
     }
     __syncthreads();
-    block_exclusive_scan<kHwThreads>(s_start, kHwBins, s_warp_scan);
+    block_exclusive_scan<THREADS>(s_start, kHwBins, s_warp_scan);
     {  // bases of every (half-warp, digit); the round's output offsets
         const int half = tid >> 8, d = tid & (kHwBins - 1);
         const uint32_t add = s_start[d] + (half ? s_half[d] : 0u);
 #pragma unroll 4
-        for (int h = half * 16; h < half * 16 + 16; ++h) s_word[h * kHwBins + d] += add;
+        for (int h = half * kPerHalf; h < half * kPerHalf + kPerHalf; ++h) s_word[h * kHwBins + d] += add;
         if (tid < kHwBins) s_delta[tid] = s_run[tid] - s_start[tid];
     }
     __syncthreads();
     // stage by digit (linear, over the tile's own buffer: its keys are in registers)
 #pragma unroll
-    for (int i = 0; i < kHwItems; ++i) {
-        const uint32_t j = (uint32_t)(hw * kHwBlock + i * 16 + l16);
+    for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t j = (uint32_t)(hw * kBlock + i * 16 + l16);
         if (FULL || j < tile_n) {
             const uint32_t pos = my_w[dreg[i]] + rank[i];
-            if (pos < (uint32_t)kHwTile) {
+            if (pos < (uint32_t)kTile) {
                 s_keys[pos] = kreg[i];
                 if constexpr (VALS) s_vals[pos] = vreg[i];
             }
@@ -526,8 +534,8 @@ __device__ __forceinline__ void hw_tile(const SweepArgs& a, K* s_keys, uint32_t*
     __syncthreads();
     K* keys_out = static_cast<K*>(a.keys_out);
 #pragma unroll
-    for (int i = 0; i < kHwItems; ++i) {
-        const uint32_t j = (uint32_t)(tid + i * kHwThreads);
+    for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t j = (uint32_t)(tid + i * THREADS);
         if (FULL || j < tile_n) {
             const K k = s_keys[j];
             const uint32_t d = (uint32_t)(k >> shift) & (kHwBins - 1);
@@ -542,20 +550,22 @@ __device__ __forceinline__ void hw_tile(const SweepArgs& a, K* s_keys, uint32_t*
     }
     {  // clear the ranking words for the next tile (16-byte stores)
         uint4* w4 = reinterpret_cast<uint4*>(s_word);
-        for (int i = tid; i < kHwGroups * kHwBins / 4; i += kHwThreads) w4[i] = make_uint4(0u, 0u, 0u, 0u);
+        for (int i = tid; i < kGroups * kHwBins / 4; i += THREADS) w4[i] = make_uint4(0u, 0u, 0u, 0u);
     }
     if (tid < kHwBins) s_run[tid] += s_tot[tid];
     __syncthreads();
 }
 
-template <typename K, bool VALS>
-__global__ void __launch_bounds__(kHwThreads, 2) k_downsweep_hw(SweepArgs a) {
-    using Cfg = HwCfg<K, VALS>;
+template <typename K, bool VALS, int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS, (THREADS == 512 && ITEMS <= 8) || THREADS == 256 ? 2 : 1)
+    k_downsweep_hw(SweepArgs a) {
+    using Cfg = HwCfg<K, VALS, THREADS, ITEMS>;
+    constexpr int kTile = Cfg::kTile, kBlock = Cfg::kBlock, kPitch = Cfg::kPitch, kGroups = Cfg::kGroups;
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     unsigned char* buf0 = smem;
     uint32_t* s_word = reinterpret_cast<uint32_t*>(smem + 2 * Cfg::kBufBytes);
-    uint32_t* s_start = s_word + kHwGroups * kHwBins;
+    uint32_t* s_start = s_word + kGroups * kHwBins;
     uint32_t* s_tot = s_start + kHwBins;
     uint32_t* s_run = s_tot + kHwBins;
     uint32_t* s_delta = s_run + kHwBins;
@@ -572,8 +582,8 @@ __global__ void __launch_bounds__(kHwThreads, 2) k_downsweep_hw(SweepArgs a) {
     if (t_begin >= t_end) return;
     const K* keys_in = static_cast<const K*>(a.keys_in);
 
-    for (int i = tid; i < kHwGroups * kHwBins; i += kHwThreads) s_word[i] = 0u;
-    for (int d = tid; d < kHwBins; d += kHwThreads) s_run[d] = a.chunk_off[(size_t)blockIdx.x * kHwBins + d];
+    for (int i = tid; i < kGroups * kHwBins; i += THREADS) s_word[i] = 0u;
+    for (int d = tid; d < kHwBins; d += THREADS) s_run[d] = a.chunk_off[(size_t)blockIdx.x * kHwBins + d];
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
@@ -581,19 +591,21 @@ __global__ void __launch_bounds__(kHwThreads, 2) k_downsweep_hw(SweepArgs a) {
     }
     __syncthreads();
 
-    auto full_bulk_tile = [&](uint32_t t) -> bool { return a.use_bulk && (size_t)(t + 1) * kHwTile <= a.n; };
-    // warp 0: lane 0 announces the bytes, then lane l copies half-warp block l
+    auto full_bulk_tile = [&](uint32_t t) -> bool { return a.use_bulk && (size_t)(t + 1) * kTile <= a.n; };
+    // warp 0: lane 0 announces the bytes, then lane l copies half-warp blocks l, l + 32, ...
     auto issue_tile = [&](uint32_t t, int b) {
         unsigned char* dst = buf0 + (size_t)b * Cfg::kBufBytes;
-        constexpr uint32_t kb = kHwBlock * sizeof(K);
-        if (lane == 0) mbar_arrive_expect_tx(&bars[b], kHwTile * (uint32_t)sizeof(K) + (VALS ? kHwTile * 4u : 0u));
+        constexpr uint32_t kb = kBlock * sizeof(K);
+        if (lane == 0) mbar_arrive_expect_tx(&bars[b], kTile * (uint32_t)sizeof(K) + (VALS ? kTile * 4u : 0u));
         __syncwarp();
         fence_proxy_async_smem();
-        bulk_load(dst + (size_t)lane * kHwPitch * sizeof(K), keys_in + (size_t)t * kHwTile + (size_t)lane * kHwBlock, kb,
-                  &bars[b]);
-        if constexpr (VALS)
-            bulk_load(dst + Cfg::kKeyBytes + (size_t)lane * kHwPitch * 4,
-                      a.vals_in + (size_t)t * kHwTile + (size_t)lane * kHwBlock, kHwBlock * 4, &bars[b]);
+        for (int g = lane; g < kGroups; g += 32) {
+            bulk_load(dst + (size_t)g * kPitch * sizeof(K), keys_in + (size_t)t * kTile + (size_t)g * kBlock, kb,
+                      &bars[b]);
+            if constexpr (VALS)
+                bulk_load(dst + Cfg::kKeyBytes + (size_t)g * kPitch * 4,
+                          a.vals_in + (size_t)t * kTile + (size_t)g * kBlock, kBlock * 4, &bars[b]);
+        }
     };
     if (warp == 0 && full_bulk_tile(t_begin)) issue_tile(t_begin, 0);
     uint32_t phase = 0u;
@@ -602,15 +614,15 @@ __global__ void __launch_bounds__(kHwThreads, 2) k_downsweep_hw(SweepArgs a) {
         if (warp == 0 && tile + 1 < t_end && full_bulk_tile(tile + 1)) issue_tile(tile + 1, b ^ 1);
         K* s_keys = reinterpret_cast<K*>(buf0 + (size_t)b * Cfg::kBufBytes);
         uint32_t* s_vals = reinterpret_cast<uint32_t*>(buf0 + (size_t)b * Cfg::kBufBytes + Cfg::kKeyBytes);
-        const uint32_t tile_base = tile * (uint32_t)kHwTile;
-        const uint32_t tile_n = min((uint32_t)kHwTile, a.n - tile_base);
+        const uint32_t tile_base = tile * (uint32_t)kTile;
+        const uint32_t tile_n = min((uint32_t)kTile, a.n - tile_base);
         bool ok = true;
         if (full_bulk_tile(tile)) {
             ok = mbar_wait_bounded(&bars[b], (phase >> b) & 1u, a.limit_ns);
             phase ^= 1u << b;
         } else {
-            for (uint32_t j = tid; j < tile_n; j += kHwThreads) {
-                const uint32_t p = (j / kHwBlock) * kHwPitch + (j % kHwBlock);
+            for (uint32_t j = tid; j < tile_n; j += THREADS) {
+                const uint32_t p = (j / kBlock) * kPitch + (j % kBlock);
                 s_keys[p] = keys_in[tile_base + j];
                 if constexpr (VALS) s_vals[p] = a.vals_in[tile_base + j];
             }
@@ -621,12 +633,12 @@ __global__ void __launch_bounds__(kHwThreads, 2) k_downsweep_hw(SweepArgs a) {
                 mbar_wait_bounded(&bars[b ^ 1], (phase >> (b ^ 1)) & 1u, a.limit_ns);
             return;
         }
-        if (tile_n == (uint32_t)kHwTile)
-            hw_tile<K, VALS, true>(a, s_keys, s_vals, s_word, s_start, s_tot, s_run, s_delta, s_half, s_warp_scan,
-                                   kHwTile);
+        if (tile_n == (uint32_t)kTile)
+            hw_tile<K, VALS, THREADS, ITEMS, true>(a, s_keys, s_vals, s_word, s_start, s_tot, s_run, s_delta, s_half,
+                                                   s_warp_scan, kTile);
         else
-            hw_tile<K, VALS, false>(a, s_keys, s_vals, s_word, s_start, s_tot, s_run, s_delta, s_half, s_warp_scan,
-                                    tile_n);
+            hw_tile<K, VALS, THREADS, ITEMS, false>(a, s_keys, s_vals, s_word, s_start, s_tot, s_run, s_delta, s_half,
+                                                    s_warp_scan, tile_n);
     }
 }
 
