@@ -418,6 +418,52 @@ def run_compare(args):
             "us_per_call": {"lsd_65536": us_lsd, "btn_1024": us_btn, "oet_1024": us_oet},
             "note": "launch-bound sizes: microseconds per call, not a roofline",
         })
+    elif args.workload == "learned64":
+        # 2^27 u64 keys uniform on [0, 2^64) (or [0, 2^48)) with payload = index:
+        # the learned first pass and on-chip finish against the plain rounds
+        bits = 48 if args.dist == "range48" else 64
+        keys, vals = workloads.wide_u64(bits=bits)
+        n = keys.size
+        kin = torch.from_numpy(keys.view(np.int64)).cuda()
+        vin = torch.from_numpy(vals.view(np.int32)).cuda()
+        kw, vw = torch.empty_like(kin), torch.empty_like(vin)
+        st = isort.LearnedStats()
+
+        def learned():
+            rc = lib.isort_learned_u64(ctypes.c_void_p(kw.data_ptr()), ctypes.c_void_p(vw.data_ptr()), n, bits,
+                                       args.nbuckets, 0, ctypes.byref(st), sp)
+            if rc != 0:
+                raise RuntimeError(f"isort_learned_u64: {isort.STATUS.get(rc, rc)}")
+
+        def plain():
+            rc = lib.isort_radix_u64(ctypes.c_void_p(kw.data_ptr()), ctypes.c_void_p(vw.data_ptr()), n, bits, 8, sp)
+            if rc != 0:
+                raise RuntimeError(f"isort_radix_u64: {isort.STATUS.get(rc, rc)}")
+
+        def reset():
+            kw.copy_(kin)
+            vw.copy_(vin)
+
+        isort.profile_read()
+        isort.profile_enable(True)
+        ms_l = _timed_inplace(learned, reset, args.steps, args.warmup, stream)
+        isort.profile_enable(False)
+        prof = isort.profile_read()
+        sk = kw[:: max(1, n // 4096)].cpu().numpy().view(np.uint64)
+        if not np.all(sk[1:] >= sk[:-1]):
+            raise RuntimeError("learned output not sorted")
+        ms_p = _timed_inplace(plain, reset, args.steps, args.warmup, stream)
+        line.update({
+            "value": args.steps * n / (ms_l * 1e-3) / 1e9, "ms_per_step": ms_l / args.steps, "dtype": "u64",
+            "config": {"workload": f"learned-bucket sort, u64 keys uniform on [0,2^{bits}) (seed 5) + u32 payload "
+                                   f"= index, n = 2^27", "l2": "inputs larger than L2; restored before each step "
+                                                               "(untimed)"},
+            "plain_lsd": {"value": args.steps * n / (ms_p * 1e-3) / 1e9, "ms_per_step": ms_p / args.steps,
+                          "call": f"isort_radix_u64, radix 2^8, {bits // 8} rounds, in place"},
+            "speedup_vs_plain": ms_p / ms_l,
+            "learned_stats": st.as_dict(),
+            "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in prof.items()},
+        })
     elif args.workload == "learned":
         n = 1 << args.log2n
         keys = workloads.skewed(args.dist, n)
@@ -426,7 +472,7 @@ def run_compare(args):
         st = isort.LearnedStats()
 
         def learned():
-            rc = lib.isort_learned(ctypes.c_void_p(kw.data_ptr()), None, n, 32, 0, 0, ctypes.byref(st), sp)
+            rc = lib.isort_learned(ctypes.c_void_p(kw.data_ptr()), None, n, 32, args.nbuckets, 0, ctypes.byref(st), sp)
             if rc != 0:
                 raise RuntimeError(f"isort_learned: {isort.STATUS.get(rc, rc)}")
 
@@ -527,10 +573,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--log2n", type=int, default=28)
     ap.add_argument("--radix-bits", type=int, default=8)
-    ap.add_argument("--workload", default="uniform", choices=["uniform", "learned", "segmented", "small"],
+    ap.add_argument("--workload", default="uniform", choices=["uniform", "learned", "learned64", "segmented", "small"],
                     help="uniform: the benchmark; learned / segmented: secondary comparisons with plain LSD; "
                          "small: the 65,536-key case and the block networks on 1,024 keys")
-    ap.add_argument("--dist", default="lognormal", choices=["zipf", "lognormal", "gmm"])
+    ap.add_argument("--nbuckets", type=int, default=0, help="learned: bucket count (0: the library's choice)")
+    ap.add_argument("--dist", default="lognormal", choices=["zipf", "lognormal", "gmm", "range48"],
+                    help="learned: key distribution; learned64: range48 for keys on [0, 2^48)")
     args = ap.parse_args()
     configure(args)
     if args.warmup < 3 and args.impl == "ours":

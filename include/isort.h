@@ -173,7 +173,7 @@ ISORT_API isort_status isort_segmented(uint32_t* keys, uint32_t* vals, const uin
  *      the bits its key range spans (a bucket of one key value is skipped).
  * The output is the stable sort of the input, whatever the model learned.
  * keys (u32), vals (optional) are device memory; nbuckets 2..16384 (0 = 4096,
- * doubled up to 16384 while n / nbuckets > 16,384);
+ * doubled up to 16384 while n / nbuckets > 16,384; for u64 keys > 8,192);
  * model 0 = the piecewise-linear CDF (1 = a small MLP: ISORT_ERR_UNSUPPORTED).
  * n < 2^18 sorts with the plain rounds. If more than half of the keys fall in
  * buckets beyond the on-chip capacity (65,536 keys) the call sorts with the
@@ -195,6 +195,10 @@ typedef struct {
 } isort_learned_stats;
 ISORT_API isort_status isort_learned(uint32_t* keys, uint32_t* vals, size_t n, int key_bits, int nbuckets, int model,
                                      isort_learned_stats* stats, void* stream);
+/* The same for u64 keys (key_bits 1..64, 0 = 64; u = key * 2^-key_bits). The
+ * buckets are finished by the on-chip split of step 4 on packed 64-bit items. */
+ISORT_API isort_status isort_learned_u64(uint64_t* keys, uint32_t* vals, size_t n, int key_bits, int nbuckets,
+                                         int model, isort_learned_stats* stats, void* stream);
 
 /* The learned path's steps, for callers that drive them and for checking:
  * isort_cdf_train: trains the model on a sorted sample (device, m u32 keys):

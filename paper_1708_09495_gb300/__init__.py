@@ -70,6 +70,7 @@ SIGNATURES = [
     ("isort_segmented", _i32, [_vp, _vp, _vp, _sz, _i32, _vp]),
     ("isort_radix_noalloc", _i32, [_vp, _vp, _sz, _i32, _i32, _vp]),
     ("isort_learned", _i32, [_vp, _vp, _sz, _i32, _i32, _i32, _vp, _vp]),
+    ("isort_learned_u64", _i32, [_vp, _vp, _sz, _i32, _i32, _i32, _vp, _vp]),
     ("isort_cdf_train", _i32, [_vp, ctypes.c_uint32, _i32, _vp, _vp, _vp, _vp, _vp]),
     ("isort_cdf_loss_grad", _i32, [_vp, ctypes.c_uint32, _vp, _vp, _vp, _vp]),
     ("isort_cdf_splitters", _i32, [_vp, _vp, _i32, _i32, _i32, _vp, _vp]),
@@ -245,11 +246,12 @@ def segmented(keys, vals, offsets, key_bits: int = 0, stream=None):
 
 
 def learned(keys, vals=None, key_bits: int = 0, nbuckets: int = 0, model: int = 0, stream=None):
-    """Learned-bucket stable sort of uint32 keys (in place). Returns the stats
-    dict. nbuckets 0 lets the library choose (4096 up to 16384 with n)."""
+    """Learned-bucket stable sort of uint32 or uint64 keys (in place). Returns
+    the stats dict. nbuckets 0 lets the library choose (4096 up to 16384 with n)."""
     st = LearnedStats()
-    _check(load().isort_learned(_ptr(keys), _ptr(vals), keys.numel(), key_bits, nbuckets, model, ctypes.byref(st),
-                                _stream(stream)), "isort_learned")
+    fn = load().isort_learned if _key_width(keys) == 32 else load().isort_learned_u64
+    _check(fn(_ptr(keys), _ptr(vals), keys.numel(), key_bits, nbuckets, model, ctypes.byref(st), _stream(stream)),
+           "isort_learned")
     return st.as_dict()
 
 

@@ -44,10 +44,30 @@ namespace isort {
 
 isort_status radix_sort_u32_device(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout, size_t n,
                                    int key_bits, int rb, cudaStream_t s);
+isort_status radix_sort_u64_device(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout, size_t n,
+                                   int key_bits, int rb, cudaStream_t s);
+isort_status segmented_finish_u64(uint64_t* keys, uint32_t* vals, const uint64_t* off, uint32_t nseg,
+                                  const uint64_t* seg_lo, const uint8_t* seg_bits, cudaStream_t s);
 isort_status segmented_finish_u32(uint32_t* keys, uint32_t* vals, const uint64_t* off, uint32_t nseg,
                                   const uint32_t* seg_lo, const uint8_t* seg_bits, cudaStream_t s);
 
 namespace {
+
+// The plain count-sort rounds (Section 3), in place.
+isort_status plain_sort(uint32_t* k, uint32_t* v, size_t n, int key_bits, cudaStream_t s) {
+    return radix_sort_u32_device(k, v, k, v, n, key_bits, 8, s);
+}
+isort_status plain_sort(uint64_t* k, uint32_t* v, size_t n, int key_bits, cudaStream_t s) {
+    return radix_sort_u64_device(k, v, k, v, n, key_bits, 8, s);
+}
+isort_status finish_buckets(uint32_t* k, uint32_t* v, const uint64_t* off, uint32_t nseg, const uint32_t* lo,
+                            const uint8_t* bits, cudaStream_t s) {
+    return segmented_finish_u32(k, v, off, nseg, lo, bits, s);
+}
+isort_status finish_buckets(uint64_t* k, uint32_t* v, const uint64_t* off, uint32_t nseg, const uint64_t* lo,
+                            const uint8_t* bits, cudaStream_t s) {
+    return segmented_finish_u64(k, v, off, nseg, lo, bits, s);
+}
 
 constexpr uint32_t kSampleSize = 1u << 16;
 constexpr uint64_t kSampleSeed = 0x5EED5EED5EEDull;
@@ -540,23 +560,43 @@ int bit_length(uint64_t v) {
     return b;
 }
 
+// Launch shape of the distribution passes: 512 x 8 for u32 keys; 256 x 8 for
+// u64 keys, whose larger buffers would otherwise leave one CTA per SM.
+template <typename K>
+struct BucketShape {
+    static constexpr int kThreads = sizeof(K) == 4 ? 512 : 256;
+    static constexpr int kItems = 8;
+    static constexpr uint32_t kTile = (uint32_t)kThreads * kItems;
+};
+
+// Sets the pass kernel's shared-memory size and returns it (per_sm: resident
+// CTAs per SM, optional).
+template <typename K, bool VALS>
+isort_status bucket_sweep_setup(int bins, size_t* smem, int* per_sm) {
+    using Sh = BucketShape<K>;
+    *smem = SweepCfg<K, VALS, Sh::kThreads, Sh::kItems>::smem_bytes(bins, false, bucket_tab_bytes());
+    if (*smem > max_smem_optin()) return ISORT_ERR_UNSUPPORTED;
+    auto kern = k_downsweep<K, VALS, Sh::kThreads, Sh::kItems, 0, BucketDigit<K>>;
+    ISORT_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem));
+    if (per_sm) {
+        ISORT_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, Sh::kThreads, *smem));
+        if (*per_sm < 1) return ISORT_ERR_UNSUPPORTED;
+    }
+    return ISORT_OK;
+}
+
 template <typename K>
 isort_status launch_bucket_sweep(const SweepArgs& a, const BucketDigit<K>& df, uint32_t chunks, bool vals,
                                  cudaStream_t s) {
-    using Cfg = SweepCfg<K, true, 512, 8>;
-    using CfgK = SweepCfg<K, false, 512, 8>;
-    const size_t tb = bucket_tab_bytes();
+    using Sh = BucketShape<K>;
+    size_t smem = 0;
     LaunchScope ls("bucket_sweep", s);
     if (vals) {
-        const size_t smem = Cfg::smem_bytes(a.bins, false, tb);
-        auto kern = k_downsweep<K, true, 512, 8, 0, BucketDigit<K>>;
-        ISORT_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<chunks, 512, smem, s>>>(a, df);
+        ISORT_TRY((bucket_sweep_setup<K, true>(a.bins, &smem, nullptr)));
+        k_downsweep<K, true, Sh::kThreads, Sh::kItems, 0, BucketDigit<K>><<<chunks, Sh::kThreads, smem, s>>>(a, df);
     } else {
-        const size_t smem = CfgK::smem_bytes(a.bins, false, tb);
-        auto kern = k_downsweep<K, false, 512, 8, 0, BucketDigit<K>>;
-        ISORT_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<chunks, 512, smem, s>>>(a, df);
+        ISORT_TRY((bucket_sweep_setup<K, false>(a.bins, &smem, nullptr)));
+        k_downsweep<K, false, Sh::kThreads, Sh::kItems, 0, BucketDigit<K>><<<chunks, Sh::kThreads, smem, s>>>(a, df);
     }
     return from_cuda(cudaGetLastError());
 }
@@ -574,18 +614,16 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
     const bool hv = vals != nullptr;
 
     // launch geometry of the distribution passes
-    using Cfg = SweepCfg<K, true, 512, 8>;
-    const uint32_t tile = 512 * 8;
+    const uint32_t tile = BucketShape<K>::kTile;
     const size_t tb = bucket_tab_bytes();
-    const size_t sweep_smem = Cfg::smem_bytes(bins, false, tb);
     const size_t census_smem = align_up((size_t)bins * 4 + align_up((size_t)B, 4) * 4, 16) + tb;
-    if (sweep_smem > max_smem_optin() || census_smem > max_smem_optin()) return ISORT_ERR_UNSUPPORTED;
+    if (census_smem > max_smem_optin()) return ISORT_ERR_UNSUPPORTED;
     int per_sm = 0;
     {
-        auto kern = k_downsweep<K, true, 512, 8, 0, BucketDigit<K>>;
-        ISORT_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem));
-        ISORT_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 512, sweep_smem));
-        if (per_sm < 1) return ISORT_ERR_UNSUPPORTED;
+        size_t sweep_smem = 0;
+        const isort_status so = hv ? bucket_sweep_setup<K, true>(bins, &sweep_smem, &per_sm)
+                                   : bucket_sweep_setup<K, false>(bins, &sweep_smem, &per_sm);
+        if (so != ISORT_OK) return so;
     }
     const uint32_t num_tiles = (uint32_t)((n + tile - 1) / tile);
     const uint32_t want = (uint32_t)per_sm * (uint32_t)sm_count();
@@ -607,7 +645,7 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
     const size_t o_split = take((size_t)B * sizeof(K)), o_bcount = take((size_t)B * 4);
     const size_t o_bpart = take((size_t)chunks * B * 4);
     const size_t o_hist = take((size_t)chunks * bins * 4), o_coff = take((size_t)chunks * bins * 4);
-    const size_t o_segoff = take((size_t)(B + 1) * 8), o_seglo = take((size_t)B * 4), o_segbits = take((size_t)B);
+    const size_t o_segoff = take((size_t)(B + 1) * 8), o_seglo = take((size_t)B * sizeof(K)), o_segbits = take((size_t)B);
     const size_t o_buf = take(n * sizeof(K) + (hv ? align_up(n * 4, 256) : 0));
     unsigned char* ws = nullptr;
     isort_status st = scratch_alloc((void**)&ws, off, s);
@@ -629,7 +667,7 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
     uint32_t* hist = reinterpret_cast<uint32_t*>(ws + o_hist);
     uint32_t* coff = reinterpret_cast<uint32_t*>(ws + o_coff);
     uint64_t* segoff = reinterpret_cast<uint64_t*>(ws + o_segoff);
-    uint32_t* seglo = reinterpret_cast<uint32_t*>(ws + o_seglo);
+    K* seglo = reinterpret_cast<K*>(ws + o_seglo);
     uint8_t* segbits = reinterpret_cast<uint8_t*>(ws + o_segbits);
     K* wk = reinterpret_cast<K*>(ws + o_buf);
     uint32_t* wv = hv ? reinterpret_cast<uint32_t*>(ws + o_buf + align_up(n * sizeof(K), 256)) : nullptr;
@@ -644,8 +682,7 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
         ce = cudaGetLastError();
         if (ce != cudaSuccess) return fail(from_cuda(ce));
     }
-    if constexpr (sizeof(K) == 4) st = radix_sort_u32_device(sample, nullptr, sample, nullptr, m, key_bits, 8, s);
-    else st = ISORT_ERR_UNSUPPORTED;
+    st = plain_sort(sample, nullptr, m, key_bits, s);
     if (st != ISORT_OK) return fail(st);
 
     // 2. train the model
@@ -716,8 +753,7 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
     stats->nbuckets = B;
     if (stats->overflow_fraction > 0.5) {
         stats->fell_back_to_lsd = 1;
-        st = radix_sort_u32_device(reinterpret_cast<uint32_t*>(keys), vals, reinterpret_cast<uint32_t*>(keys), vals, n,
-                                   key_bits, 8, s);
+        st = plain_sort(keys, vals, n, key_bits, s);
         scratch_free(ws, s);
         return st;
     }
@@ -780,7 +816,7 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
     // 6. finish every bucket on the bits its key range spans; buckets beyond
     // the on-chip capacity are sorted by the plain rounds, one at a time
     std::vector<uint64_t> h_off(B + 1);
-    std::vector<uint32_t> h_lo(B);
+    std::vector<K> h_lo(B);
     std::vector<uint8_t> h_bits(B);
     std::vector<int> big;
     h_off[0] = 0;
@@ -789,7 +825,7 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
         h_off[b + 1] = h_off[b] + h_count[b];
         const uint64_t lo = b == 0 ? 0 : (uint64_t)h_split[b];
         const uint64_t hi_incl = b + 1 < B ? (uint64_t)h_split[b + 1] - (h_split[b + 1] > 0 ? 1 : 0) : kmax;
-        h_lo[b] = (uint32_t)lo;
+        h_lo[b] = (K)lo;
         const uint64_t span = hi_incl >= lo ? hi_incl - lo : 0;
         h_bits[b] = (uint8_t)bit_length(span);
         if (h_count[b] > kOnChipCapacity && h_bits[b] > 0) {
@@ -798,19 +834,13 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
         }
     }
     ce = cudaMemcpyAsync(segoff, h_off.data(), (size_t)(B + 1) * 8, cudaMemcpyHostToDevice, s);
-    if (ce == cudaSuccess) ce = cudaMemcpyAsync(seglo, h_lo.data(), (size_t)B * 4, cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(seglo, h_lo.data(), (size_t)B * sizeof(K), cudaMemcpyHostToDevice, s);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(segbits, h_bits.data(), (size_t)B, cudaMemcpyHostToDevice, s);
     if (ce != cudaSuccess) return fail(from_cuda(ce));
-    if constexpr (sizeof(K) == 4) {
-        st = segmented_finish_u32(reinterpret_cast<uint32_t*>(keys), vals, segoff, (uint32_t)B, seglo, segbits, s);
-        for (size_t i = 0; i < big.size() && st == ISORT_OK; ++i) {
-            const int b = big[i];
-            uint32_t* k = reinterpret_cast<uint32_t*>(keys) + h_off[b];
-            uint32_t* v = hv ? vals + h_off[b] : nullptr;
-            st = radix_sort_u32_device(k, v, k, v, h_count[b], key_bits, 8, s);
-        }
-    } else {
-        st = ISORT_ERR_UNSUPPORTED;
+    st = finish_buckets(keys, vals, segoff, (uint32_t)B, seglo, segbits, s);
+    for (size_t i = 0; i < big.size() && st == ISORT_OK; ++i) {
+        const int b = big[i];
+        st = plain_sort(keys + h_off[b], hv ? vals + h_off[b] : nullptr, h_count[b], key_bits, s);
     }
     if (st != ISORT_OK) return fail(st);
     st = finish_status(status, s);
@@ -823,20 +853,24 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
 
 using namespace isort;
 
-extern "C" {
+namespace {
 
-isort_status isort_learned(uint32_t* keys, uint32_t* vals, size_t n, int key_bits, int nbuckets, int model,
+template <typename K>
+isort_status learned_entry(K* keys, uint32_t* vals, size_t n, int key_bits, int nbuckets, int model,
                            isort_learned_stats* stats, void* stream) {
+    constexpr int kw = (int)sizeof(K) * 8;
     isort_learned_stats local;
     isort_learned_stats* st = stats ? stats : &local;
     std::memset(st, 0, sizeof(*st));
-    if (key_bits == 0) key_bits = 32;
-    if (key_bits < 1 || key_bits > 32) return ISORT_ERR_INVALID_ARG;
+    if (key_bits == 0) key_bits = kw;
+    if (key_bits < 1 || key_bits > kw) return ISORT_ERR_INVALID_ARG;
     if (nbuckets == 0) {
         // 4096 buckets, doubled (up to the table limit) while the mean bucket
-        // would exceed a quarter of the on-chip capacity
+        // would exceed a quarter of the on-chip capacity (u32) or one CTA's
+        // 8,192 keys (u64, whose clusters cost more per key)
+        const uint64_t mean_max = sizeof(K) == 4 ? kOnChipCapacity / 4 : kOnChipCapacity / 8;
         nbuckets = 4096;
-        while (nbuckets < kMaxBuckets && (uint64_t)nbuckets * (kOnChipCapacity / 4) < n) nbuckets <<= 1;
+        while (nbuckets < kMaxBuckets && (uint64_t)nbuckets * mean_max < n) nbuckets <<= 1;
     }
     if (nbuckets < 2 || nbuckets > kMaxBuckets) return ISORT_ERR_INVALID_ARG;
     if (model != 0 && model != 1) return ISORT_ERR_INVALID_ARG;
@@ -849,9 +883,24 @@ isort_status isort_learned(uint32_t* keys, uint32_t* vals, size_t n, int key_bit
     if (n < (size_t)4 * kSampleSize) {
         // too few keys for a sample to pay off: the plain rounds
         st->fell_back_to_lsd = 1;
-        return radix_sort_u32_device(keys, vals, keys, vals, n, key_bits, 8, s);
+        return plain_sort(keys, vals, n, key_bits, s);
     }
-    return learned_device<uint32_t>(keys, vals, n, key_bits, nbuckets, st, s);
+    return learned_device<K>(keys, vals, n, key_bits, nbuckets, st, s);
+}
+
+}  // namespace
+
+
+extern "C" {
+
+isort_status isort_learned(uint32_t* keys, uint32_t* vals, size_t n, int key_bits, int nbuckets, int model,
+                           isort_learned_stats* stats, void* stream) {
+    return learned_entry<uint32_t>(keys, vals, n, key_bits, nbuckets, model, stats, stream);
+}
+
+isort_status isort_learned_u64(uint64_t* keys, uint32_t* vals, size_t n, int key_bits, int nbuckets, int model,
+                               isort_learned_stats* stats, void* stream) {
+    return learned_entry<uint64_t>(keys, vals, n, key_bits, nbuckets, model, stats, stream);
 }
 
 isort_status isort_cdf_splitters(const float* X, const float* Y, int key_width, int key_bits, int nbuckets,

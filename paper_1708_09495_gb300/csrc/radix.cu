@@ -1304,6 +1304,12 @@ isort_status radix_sort_u32_device(const uint32_t* kin, const uint32_t* vin, uin
     return radix_device<uint32_t>(kin, vin, kout, vout, n, key_bits, rb, s);
 }
 
+isort_status radix_sort_u64_device(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout, size_t n,
+                                   int key_bits, int rb, cudaStream_t s) {
+    if (key_bits == 0) key_bits = 64;
+    return radix_device<uint64_t>(kin, vin, kout, vout, n, key_bits, rb, s);
+}
+
 // Scratch an in-place sort of n u32 keys (+ payload) needs when the caller
 // provides it: the control block followed by the ping-pong buffers.
 size_t radix_u32_inplace_workspace_bytes(size_t n, int key_bits, int rb, bool vals) {

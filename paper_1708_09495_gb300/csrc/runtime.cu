@@ -2,6 +2,7 @@
 // per-kernel event timing.
 #include <atomic>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -175,8 +176,23 @@ thread_local int t_capturing = 0;
 CaptureScope::CaptureScope() { ++t_capturing; }
 CaptureScope::~CaptureScope() { --t_capturing; }
 
+// ISORT_TRACE=1: every launch scope names itself on stderr as it opens and,
+// outside stream capture, waits for its work when it closes (a debugging aid
+// that shows which step a stalled call is in).
+bool trace_on() {
+    static const bool on = [] {
+        const char* e = std::getenv("ISORT_TRACE");
+        return e && e[0] == '1';
+    }();
+    return on;
+}
+
 LaunchScope::LaunchScope(const char* name, cudaStream_t s, bool count) : name_(name), s_(s) {
     if (count) g_launches.fetch_add(1);
+    if (trace_on()) {
+        std::fprintf(stderr, "[isort] %s\n", name);
+        std::fflush(stderr);
+    }
     if (g_profile.load() && t_capturing == 0) {
         if (cudaEventCreate(&e0_) == cudaSuccess) cudaEventRecord(e0_, s_);
         else e0_ = nullptr;
@@ -184,6 +200,11 @@ LaunchScope::LaunchScope(const char* name, cudaStream_t s, bool count) : name_(n
 }
 
 LaunchScope::~LaunchScope() {
+    if (trace_on() && t_capturing == 0) {
+        const cudaError_t e = cudaStreamSynchronize(s_);
+        std::fprintf(stderr, "[isort] %s done (%s)\n", name_, cudaGetErrorString(e));
+        std::fflush(stderr);
+    }
     if (!e0_) return;
     cudaEvent_t e1 = nullptr;
     if (cudaEventCreate(&e1) != cudaSuccess) {

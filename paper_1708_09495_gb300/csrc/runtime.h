@@ -25,6 +25,9 @@ int64_t peek_stall_tile();      // the injected stall without consuming it
 // in synchronous mode waits for `s` and maps the bits to a status; in
 // asynchronous mode folds them into the device's sticky status word.
 isort_status finish_status(const uint32_t* d_status, cudaStream_t s);
+// ISORT_TRACE=1 in the environment: launches are named on stderr and waited for.
+bool trace_on();
+
 // The status of a device status word already read on the host.
 isort_status map_bits(uint32_t v);
 

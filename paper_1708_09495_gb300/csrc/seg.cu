@@ -143,17 +143,19 @@ __global__ void __launch_bounds__(P) k_seg_btn_cta(uint32_t* keys, uint32_t* val
     }
 }
 
-struct ClusterArgs {
-    uint32_t* keys;
+template <typename K>
+struct SegArgsT {
+    K* keys;
     uint32_t* vals;
     const uint64_t* off;
     const uint32_t* list;
     SegCtl* ctl;
     int cls;
     int key_bits;
-    const uint32_t* seg_lo;   // optional: segment s's keys lie in [seg_lo[s], seg_lo[s] + 2^seg_bits[s])
+    const K* seg_lo;          // optional: segment s's keys lie in [seg_lo[s], seg_lo[s] + 2^seg_bits[s])
     const uint8_t* seg_bits;  //   and are sorted on key - seg_lo[s] over seg_bits[s] bits
 };
+using ClusterArgs = SegArgsT<uint32_t>;
 
 constexpr size_t cluster_smem_bytes(bool vals) {
     return (size_t)kSegChunk * 4 * (vals ? 2 : 1) + (size_t)kSegWarps * kSegBins * 2 + (size_t)kSegBins * 4 * 3 +
@@ -359,15 +361,17 @@ __global__ void __launch_bounds__(kSegThreads, 2) k_seg_cluster(ClusterArgs a) {
 // work stack kept identically by every CTA of the cluster), so a group is
 // either finished by a warp, or holds one key value.
 constexpr int kSplitWarpMax = 512;  // longest group a warp finishes (BTN, 16 keys per lane)
-constexpr int kSplitStack = 512;    // pending groups; bound: 4 levels x 65536 / 513
+// Pending groups: they are disjoint parts of one segment (<= 65,536 keys) and
+// each holds more than 256 keys, so at most 255 are pending at once.
+constexpr int kSplitStack = 512;
 
-__host__ __device__ constexpr size_t split_smem_bytes(bool vals, int bins) {
-    return (size_t)kSegChunk * 4 * (vals ? 2 : 1)  // staging
-           + (size_t)kSegWarps * bins * 2           // per-warp digit counts
-           + (size_t)kSegWarps * bins * 4           // per-warp peer masks
-           + (size_t)bins * 4 * 5 + 4 * 4           // cta totals, earlier CTAs, base, local start, starts[bins+1]
-           + 64 * 4                                 // misc
-           + (size_t)kSplitStack * 13;              // work stack
+__host__ __device__ constexpr size_t split_smem_bytes(bool vals, int bins, size_t key_bytes = 4) {
+    return (size_t)kSegChunk * (key_bytes + (vals ? 4 : 0))  // staging
+           + (size_t)kSegWarps * bins * 2                    // per-warp digit counts
+           + (size_t)kSegWarps * bins * 4                    // per-warp peer masks
+           + (size_t)bins * 4 * 5 + 4 * 4                    // cta totals, earlier CTAs, base, local start, starts[bins+1]
+           + 64 * 4 + 16                                     // misc (+ alignment)
+           + (size_t)kSplitStack * (9 + key_bytes);          // work stack
 }
 
 // Exclusive scan of a[0..BINS-1] in place (threads 0..BINS-1, BINS <= 512;
@@ -408,33 +412,33 @@ __device__ __forceinline__ void btn_warp_fill(uint32_t* k, uint32_t* v, uint32_t
 // ib = bit_length(len) so that every item is below the pad 0xFFFFFFFF (keys
 // only: no index, ib = 0). Needs shift + ib <= 32, shift the bits the group's
 // keys span above gkb.
-template <int B, bool VALS>
-__device__ __forceinline__ void btn_warp_packed(uint32_t* k, uint32_t* v, uint32_t len, uint32_t gkb, int ib) {
+template <int B, bool VALS, typename K>
+__device__ __forceinline__ void btn_warp_packed(K* k, uint32_t* v, uint32_t len, K gkb, int ib) {
     const int t = threadIdx.x & 31;
     int p = 1;
     while ((uint32_t)(p * B) < len) p <<= 1;
-    uint32_t x[B];
+    K x[B];
 #pragma unroll
     for (int i = 0; i < B; ++i) {
         const uint32_t g = (uint32_t)t * B + i;
-        x[i] = g < len ? (((k[g] - gkb) << ib) | (VALS ? g : 0u)) : 0xFFFFFFFFu;
+        x[i] = g < len ? (((k[g] - gkb) << ib) | (VALS ? (K)g : (K)0)) : ~(K)0;
     }
-    net::local_sort<B, uint32_t>(x);
+    net::local_sort<B, K>(x);
     for (int kk = 2; kk <= p; kk <<= 1) {
         for (int j = kk >> 1; j > 0; j >>= 1) {
             const bool asc = (t & kk) == 0;
             const bool lower = t < (t ^ j);
-            net::merge_split_shfl<B, uint32_t>(x, j, lower == asc);
-            net::bitonic_merge<B, uint32_t>(x);
+            net::merge_split_shfl<B, K>(x, j, lower == asc);
+            net::bitonic_merge<B, K>(x);
         }
     }
     uint32_t vv[B];
     if constexpr (VALS) {
-        const uint32_t m = (1u << ib) - 1u;
+        const K m = ((K)1 << ib) - (K)1;
 #pragma unroll
         for (int i = 0; i < B; ++i) {
             const uint32_t g = (uint32_t)t * B + i;
-            vv[i] = g < len ? v[x[i] & m] : 0u;
+            vv[i] = g < len ? v[(uint32_t)(x[i] & m)] : 0u;
         }
     }
     __syncwarp();  // every payload is read before any is written
@@ -448,34 +452,53 @@ __device__ __forceinline__ void btn_warp_packed(uint32_t* k, uint32_t* v, uint32
     }
 }
 
-template <bool VALS>
-__device__ __forceinline__ void finish_group_warp(uint32_t* k, uint32_t* v, uint32_t len, uint32_t gkb, int shift) {
+// A group of len keys spanning `shift` bits above its base packs into one item
+// of the key's width when the index fits beside the key bits.
+template <bool VALS, typename K>
+__device__ __forceinline__ bool group_packs(uint32_t len, int shift) {
     const int ib = VALS ? 32 - __clz(len) : 0;
-    if (shift + ib <= 32) {
-        if (len <= 32) btn_warp_packed<1, VALS>(k, v, len, gkb, ib);
-        else if (len <= 64) btn_warp_packed<2, VALS>(k, v, len, gkb, ib);
-        else if (len <= 128) btn_warp_packed<4, VALS>(k, v, len, gkb, ib);
-        else if (len <= 256) btn_warp_packed<8, VALS>(k, v, len, gkb, ib);
-        else btn_warp_packed<16, VALS>(k, v, len, gkb, ib);
+    return shift + ib <= (int)sizeof(K) * 8;
+}
+
+// Whether a warp can finish the group: packed items, or (u32 keys) the 64-bit
+// (key, index) items of the block networks. A u64 group that does not pack is
+// split again instead.
+template <bool VALS, typename K>
+__device__ __forceinline__ bool group_warp_ok(uint32_t len, int shift) {
+    return len <= (uint32_t)kSplitWarpMax && (sizeof(K) == 4 || group_packs<VALS, K>(len, shift));
+}
+
+template <bool VALS, typename K>
+__device__ __forceinline__ void finish_group_warp(K* k, uint32_t* v, uint32_t len, K gkb, int shift) {
+    const int ib = VALS ? 32 - __clz(len) : 0;
+    if (group_packs<VALS, K>(len, shift)) {
+        if (len <= 32) btn_warp_packed<1, VALS, K>(k, v, len, gkb, ib);
+        else if (len <= 64) btn_warp_packed<2, VALS, K>(k, v, len, gkb, ib);
+        else if (len <= 128) btn_warp_packed<4, VALS, K>(k, v, len, gkb, ib);
+        else if (len <= 256) btn_warp_packed<8, VALS, K>(k, v, len, gkb, ib);
+        else btn_warp_packed<16, VALS, K>(k, v, len, gkb, ib);
         return;
     }
-    if (len <= 32) btn_warp_fill<1>(k, v, len);
-    else if (len <= 64) btn_warp_fill<2>(k, v, len);
-    else if (len <= 128) btn_warp_fill<4>(k, v, len);
-    else if (len <= 256) btn_warp_fill<8>(k, v, len);
-    else btn_warp_fill<16>(k, v, len);
+    if constexpr (sizeof(K) == 4) {
+        if (len <= 32) btn_warp_fill<1>(k, v, len);
+        else if (len <= 64) btn_warp_fill<2>(k, v, len);
+        else if (len <= 128) btn_warp_fill<4>(k, v, len);
+        else if (len <= 256) btn_warp_fill<8>(k, v, len);
+        else btn_warp_fill<16>(k, v, len);
+    }
 }
 
 // RB: the split's digit width (8, or 9 where groups of about 128 keys let
 // payload items pack into 32 bits).
-template <int C, bool VALS, int RB>
-__global__ void __launch_bounds__(kSegThreads, RB == 8 ? 2 : 1) k_seg_split(ClusterArgs a) {
+template <int C, bool VALS, int RB, typename K>
+__global__ void __launch_bounds__(kSegThreads, (RB == 8 && sizeof(K) == 4) ? 2 : 1) k_seg_split(SegArgsT<K> a) {
     constexpr int BINS = 1 << RB;
+    constexpr int KW = (int)sizeof(K) * 8;
     static_assert(BINS <= kSegThreads, "one thread per digit");
     extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t* s_keys = reinterpret_cast<uint32_t*>(smem);
-    uint32_t* s_vals = s_keys + kSegChunk;
-    uint16_t* s_cnt = reinterpret_cast<uint16_t*>(s_keys + kSegChunk * (VALS ? 2 : 1));
+    K* s_keys = reinterpret_cast<K*>(smem);
+    uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + kSegChunk);
+    uint16_t* s_cnt = reinterpret_cast<uint16_t*>(smem + (size_t)kSegChunk * (sizeof(K) + (VALS ? 4 : 0)));
     uint32_t* s_match = reinterpret_cast<uint32_t*>(s_cnt + kSegWarps * BINS);
     uint32_t* s_cta = s_match + kSegWarps * BINS;  // this CTA's digit totals
     uint32_t* s_pre = s_cta + BINS;                 // the digit's keys in lower-ranked CTAs
@@ -483,10 +506,11 @@ __global__ void __launch_bounds__(kSegThreads, RB == 8 ? 2 : 1) k_seg_split(Clus
     uint32_t* s_lst = s_base + BINS;                // local start of the digit in the staging buffer
     uint32_t* s_start = s_lst + BINS;               // [BINS+1] group-relative digit starts (same in every CTA)
     uint32_t* s_misc = s_start + BINS + 4;          // [1] range flag, [2] stack size, [8..23] warp sums
-    uint32_t* st_lo = s_misc + 64;                      // work stack: group start (segment-relative)
+    // work stack: group key base, start (segment-relative), length, span bits
+    K* st_kb = reinterpret_cast<K*>(align_up_dev(reinterpret_cast<uintptr_t>(s_misc + 64), sizeof(K)));
+    uint32_t* st_lo = reinterpret_cast<uint32_t*>(st_kb + kSplitStack);
     uint32_t* st_len = st_lo + kSplitStack;
-    uint32_t* st_kb = st_len + kSplitStack;
-    uint8_t* st_bits = reinterpret_cast<uint8_t*>(st_kb + kSplitStack);
+    uint8_t* st_bits = reinterpret_cast<uint8_t*>(st_len + kSplitStack);
     if ((size_t)(st_bits + kSplitStack - smem) > dynamic_smem_size()) {
         if (threadIdx.x == 0) set_status(&a.ctl->status, kStatBounds);
         return;  // every CTA of the cluster sees the same size: all leave
@@ -507,40 +531,49 @@ __global__ void __launch_bounds__(kSegThreads, RB == 8 ? 2 : 1) k_seg_split(Clus
         const uint32_t s = a.list[q];
         const uint64_t seg0 = a.off[s];
         const uint32_t L = (uint32_t)(a.off[s + 1] - seg0);
-        const int check_bits = a.seg_bits ? 32 : a.key_bits;
+        const int check_bits = a.seg_bits ? KW : a.key_bits;
         if (tid == 0) {
             st_lo[0] = 0;
             st_len[0] = L;
-            st_kb[0] = a.seg_lo ? a.seg_lo[s] : 0u;
+            st_kb[0] = a.seg_lo ? a.seg_lo[s] : (K)0;
             st_bits[0] = (uint8_t)(a.seg_bits ? (int)a.seg_bits[s] : a.key_bits);
             s_misc[2] = 1;
         }
         __syncthreads();
         bool first = true;
+        // every pop removes a group and pushes only narrower ones, so the loop
+        // ends; the bound (identical in every CTA) only guards that reasoning
+        int guard = 0;
         while (s_misc[2] > 0) {
+            if (++guard > 4 * kSplitStack) {
+                if (tid == 0 && r == 0) set_status(&a.ctl->status, kStatBounds);
+                break;
+            }
             // pop (identically in every CTA)
             const uint32_t top = s_misc[2] - 1;
-            const uint32_t g_lo = st_lo[top], g_len = st_len[top], kb = st_kb[top];
+            const uint32_t g_lo = st_lo[top], g_len = st_len[top];
+            const K kb = st_kb[top];
             const int bits = st_bits[top];
             __syncthreads();
             if (tid == 0) s_misc[2] = top;
             const int shift = bits > RB ? bits - RB : 0;
             const uint32_t my_lo = r * (uint32_t)kSegChunk;
             const uint32_t my_n = g_len > my_lo ? min(g_len - my_lo, (uint32_t)kSegChunk) : 0u;
-            uint32_t* gk = a.keys + seg0 + g_lo;
+            K* gk = a.keys + seg0 + g_lo;
             uint32_t* gv = VALS ? a.vals + seg0 + g_lo : nullptr;
 
-            uint32_t k[kSegItems], v[kSegItems], rank[kSegItems];
-            uint32_t orv = 0;
+            K k[kSegItems];
+            uint32_t v[kSegItems], rank[kSegItems];
+            K orv = 0;
 #pragma unroll
             for (int i = 0; i < kSegItems; ++i) {
                 const uint32_t j = (uint32_t)(warp * kSegItems * 32 + i * 32 + lane);
-                k[i] = j < my_n ? gk[my_lo + j] : 0u;
+                k[i] = j < my_n ? gk[my_lo + j] : (K)0;
                 if constexpr (VALS) v[i] = j < my_n ? gv[my_lo + j] : 0u;
                 orv |= k[i];
             }
             if (first) {
-                const int bad = __syncthreads_or(check_bits < 32 && (orv >> check_bits) != 0);
+                const int bad = __syncthreads_or(check_bits < KW && (orv >> check_bits) != 0);
                 if (tid == 0) s_misc[1] = (uint32_t)bad;
             }
             // rank among equal digits of the warp, in input order (peer masks)
@@ -548,7 +581,7 @@ __global__ void __launch_bounds__(kSegThreads, RB == 8 ? 2 : 1) k_seg_split(Clus
             for (int i = 0; i < kSegItems; ++i) {
                 const uint32_t j = (uint32_t)(warp * kSegItems * 32 + i * 32 + lane);
                 const bool valid = j < my_n;
-                const uint32_t dg = ((k[i] - kb) >> shift) & (uint32_t)(BINS - 1);
+                const uint32_t dg = (uint32_t)((k[i] - kb) >> shift) & (uint32_t)(BINS - 1);
                 uint32_t* mw = &s_match[warp * BINS + dg];
                 if (valid) atomicOr(mw, 1u << lane);
                 __syncwarp();
@@ -576,7 +609,7 @@ __global__ void __launch_bounds__(kSegThreads, RB == 8 ? 2 : 1) k_seg_split(Clus
                 s_lst[tid] = sum;
             }
             cluster.sync();  // (A) every CTA's totals and range flag are visible
-            if (first && check_bits < 32) {
+            if (first && check_bits < KW) {
                 uint32_t any = 0;
                 for (int rr = 0; rr < C; ++rr) any |= C == 1 ? s_misc[1] : *cluster.map_shared_rank(&s_misc[1], rr);
                 if (any) {  // the whole cluster leaves the segment unchanged
@@ -608,7 +641,7 @@ __global__ void __launch_bounds__(kSegThreads, RB == 8 ? 2 : 1) k_seg_split(Clus
             for (int i = 0; i < kSegItems; ++i) {
                 const uint32_t j = (uint32_t)(warp * kSegItems * 32 + i * 32 + lane);
                 if (j < my_n) {
-                    const uint32_t dg = ((k[i] - kb) >> shift) & (uint32_t)(BINS - 1);
+                    const uint32_t dg = (uint32_t)((k[i] - kb) >> shift) & (uint32_t)(BINS - 1);
                     const uint32_t p = s_lst[dg] + s_cnt[warp * BINS + dg] + rank[i];
                     s_keys[p] = k[i];
                     if constexpr (VALS) s_vals[p] = v[i];
@@ -616,8 +649,8 @@ __global__ void __launch_bounds__(kSegThreads, RB == 8 ? 2 : 1) k_seg_split(Clus
             }
             __syncthreads();
             for (uint32_t j = tid; j < my_n; j += kSegThreads) {
-                const uint32_t key = s_keys[j];
-                const uint32_t dg = ((key - kb) >> shift) & (uint32_t)(BINS - 1);
+                const K key = s_keys[j];
+                const uint32_t dg = (uint32_t)((key - kb) >> shift) & (uint32_t)(BINS - 1);
                 const uint32_t o = s_base[dg] + (j - s_lst[dg]);
                 gk[o] = key;
                 if constexpr (VALS) gv[o] = s_vals[j];
@@ -628,23 +661,22 @@ __global__ void __launch_bounds__(kSegThreads, RB == 8 ? 2 : 1) k_seg_split(Clus
             if (shift > 0) {
                 for (int d = (int)r * kSegWarps + warp; d < BINS; d += C * kSegWarps) {
                     const uint32_t c0 = s_start[d], c1 = s_start[d + 1], len = c1 - c0;
-                    if (len <= 1 || len > (uint32_t)kSplitWarpMax) continue;
-                    finish_group_warp<VALS>(gk + c0, VALS ? gv + c0 : nullptr, len, kb + ((uint32_t)d << shift),
-                                            shift);
+                    if (len <= 1 || !group_warp_ok<VALS, K>(len, shift)) continue;
+                    finish_group_warp<VALS, K>(gk + c0, VALS ? gv + c0 : nullptr, len, kb + ((K)d << shift), shift);
                 }
                 if (warp == 0) {  // push the groups above a warp's reach, in digit order
                     uint32_t top2 = s_misc[2];
                     for (int d0 = 0; d0 < BINS; d0 += 32) {
                         const int d = d0 + lane;
                         const uint32_t len = s_start[d + 1] - s_start[d];
-                        const bool big = len > (uint32_t)kSplitWarpMax;
+                        const bool big = len > 1 && !group_warp_ok<VALS, K>(len, shift);
                         const uint32_t m = __ballot_sync(kFullMask, big);
                         const uint32_t slot = top2 + (uint32_t)__popc(m & lanemask_lt());
                         if (big) {
                             if (slot < (uint32_t)kSplitStack) {
                                 st_lo[slot] = g_lo + s_start[d];
                                 st_len[slot] = len;
-                                st_kb[slot] = kb + ((uint32_t)d << shift);
+                                st_kb[slot] = kb + ((K)d << shift);
                                 st_bits[slot] = (uint8_t)shift;
                             } else {  // cannot happen (see kSplitStack)
                                 set_status(&a.ctl->status, kStatBounds);
@@ -657,6 +689,10 @@ __global__ void __launch_bounds__(kSegThreads, RB == 8 ? 2 : 1) k_seg_split(Clus
             }
             __syncthreads();
         }
+        // every thread has read the empty stack before thread 0 starts the next
+        // segment's stack (without this a slow warp could see the new size and
+        // run one more round of the old segment, out of step with the cluster)
+        __syncthreads();
     }
     cluster.sync();  // no CTA leaves while others may still read its shared memory
 }
@@ -708,13 +744,13 @@ isort_status launch_btn_cta(uint32_t* keys, uint32_t* vals, const uint64_t* off,
     return from_cuda(cudaGetLastError());
 }
 
-template <int C>
-isort_status launch_split(bool vals, const ClusterArgs& a, cudaStream_t s) {
-    // payload groups pack into 32-bit items when the index fits next to the
-    // key's remaining bits: 9-bit digits for the largest segments
-    constexpr int kRbVals = C == 8 ? 9 : 8;
-    const size_t smem = split_smem_bytes(vals, vals ? 1 << kRbVals : 256);
-    auto kern = vals ? k_seg_split<C, true, kRbVals> : k_seg_split<C, false, 8>;
+template <int C, typename K = uint32_t>
+isort_status launch_split(bool vals, const SegArgsT<K>& a, cudaStream_t s) {
+    // u32 payload groups pack into 32-bit items when the index fits next to
+    // the key's remaining bits: 9-bit digits for the largest segments
+    constexpr int kRbVals = (C == 8 && sizeof(K) == 4) ? 9 : 8;
+    const size_t smem = split_smem_bytes(vals, vals ? 1 << kRbVals : 256, sizeof(K));
+    auto kern = vals ? k_seg_split<C, true, kRbVals, K> : k_seg_split<C, false, 8, K>;
     ISORT_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -732,7 +768,7 @@ isort_status launch_split(bool vals, const ClusterArgs& a, cudaStream_t s) {
     ISORT_TRY_CUDA(cudaOccupancyMaxActiveClusters(&clusters, (void*)kern, &cfg));
     if (clusters < 1) return ISORT_ERR_UNSUPPORTED;
     cfg.gridDim = dim3(C * clusters);
-    LaunchScope ls(C == 2 ? "seg_split2" : C == 4 ? "seg_split4" : "seg_split8", s);
+    LaunchScope ls(C == 1 ? "seg_split1" : C == 2 ? "seg_split2" : C == 4 ? "seg_split4" : "seg_split8", s);
     ISORT_TRY_CUDA(cudaLaunchKernelEx(&cfg, kern, a));
     return ISORT_OK;
 }
@@ -876,8 +912,8 @@ isort_status segmented_entry(uint32_t* keys, uint32_t* vals, const uint64_t* off
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(s, &cap);
     const int big_ok = sync_mode() && cap != cudaStreamCaptureStatusActive;
-    if (cap == cudaStreamCaptureStatusActive) {
-        // the caller is building its own graph: enqueue directly
+    if (cap == cudaStreamCaptureStatusActive || trace_on()) {
+        // the caller is building its own graph (or launches are traced): enqueue directly
         st = enqueue_segmented(keys, vals, off, ns, key_bits, ctl, lists, big_ok, s, seg_lo, seg_bits);
     } else {
         st = launch_via_graph(keys, vals, off, ns, key_bits, ctl, lists, big_ok, s, seg_lo, seg_bits);
@@ -928,6 +964,56 @@ isort_status segmented_entry(uint32_t* keys, uint32_t* vals, const uint64_t* off
 isort_status segmented_finish_u32(uint32_t* keys, uint32_t* vals, const uint64_t* off, uint32_t nseg,
                                   const uint32_t* seg_lo, const uint8_t* seg_bits, cudaStream_t s) {
     return segmented_entry(keys, vals, off, nseg, 32, (void*)s, seg_lo, seg_bits);
+}
+
+// The same for u64 keys, segments of at most 8 x 8192 keys: every segment of
+// two or more keys (and more than one key value) goes to the split kernel of
+// its size class (one CTA up to 8192 keys, then clusters of 2, 4, 8), whose
+// warps finish the digit groups on packed 64-bit items. Synchronises.
+isort_status segmented_finish_u64(uint64_t* keys, uint32_t* vals, const uint64_t* off, uint32_t nseg,
+                                  const uint64_t* seg_lo, const uint8_t* seg_bits, cudaStream_t s) {
+    if (nseg == 0) return ISORT_OK;
+    const size_t ctl_bytes = align_up(sizeof(SegCtl), 256);
+    const size_t list_bytes = align_up((size_t)kNumCls * nseg * 4, 256);
+    unsigned char* ws = nullptr;
+    isort_status st = scratch_alloc((void**)&ws, ctl_bytes + list_bytes, s);
+    if (st != ISORT_OK) return st;
+    SegCtl* ctl = reinterpret_cast<SegCtl*>(ws);
+    uint32_t* lists = reinterpret_cast<uint32_t*>(ws + ctl_bytes);
+    cudaError_t ce = cudaMemsetAsync(ctl, 0, sizeof(SegCtl), s);
+    if (ce == cudaSuccess) {
+        LaunchScope ls("seg_classify", s);
+        const SegThresholds none{0, 0, 0};  // no network classes: the split kernels take every length
+        const unsigned grid = (unsigned)std::max<uint32_t>(1, std::min<uint32_t>((nseg + 255) / 256, 4 * sm_count()));
+        k_seg_classify<<<grid, 256, 0, s>>>(off, nseg, none, ctl, lists, 0, seg_bits);
+        ce = cudaGetLastError();
+    }
+    if (ce != cudaSuccess) {
+        scratch_free(ws, s);
+        return from_cuda(ce);
+    }
+    SegArgsT<uint64_t> a;
+    a.keys = keys;
+    a.vals = vals;
+    a.off = off;
+    a.ctl = ctl;
+    a.key_bits = 64;
+    a.seg_lo = seg_lo;
+    a.seg_bits = seg_bits;
+    const bool v = vals != nullptr;
+    const int order[4] = {kClsC8, kClsC4, kClsC2, kClsC1};
+    for (int c : order) {
+        a.cls = c;
+        a.list = lists + (size_t)c * nseg;
+        st = c == kClsC8   ? launch_split<8, uint64_t>(v, a, s)
+             : c == kClsC4 ? launch_split<4, uint64_t>(v, a, s)
+             : c == kClsC2 ? launch_split<2, uint64_t>(v, a, s)
+                           : launch_split<1, uint64_t>(v, a, s);
+        if (st != ISORT_OK) break;
+    }
+    if (st == ISORT_OK) st = finish_status(&ctl->status, s);  // a longer segment sets "unsupported"
+    scratch_free(ws, s);
+    return st;
 }
 
 }  // namespace isort

@@ -73,6 +73,49 @@ def test_learned_full_size_keys_only(cuda_lib, kind):
         assert st["nbuckets"] == 16384 and not st["fell_back_to_lsd"]
 
 
+def _u64_vs_oracle(isort, keys, vals=True, key_bits=0):
+    v = gen.iota_u32(keys.size) if vals else None
+    dk = to_dev(keys)
+    dv = to_dev(v) if vals else None
+    st = isort.learned(dk, dv, key_bits=key_bits)
+    ek, ev = oracle.lsd(keys, v, key_bits=key_bits, radix_bits=8)
+    assert np.array_equal(to_np(dk, np.uint64), ek)
+    if vals:
+        assert np.array_equal(to_np(dv, np.uint32), ev)
+    return st
+
+
+@pytest.mark.parametrize("bits", [64, 48])
+def test_learned_u64_uniform(cuda_lib, bits):
+    keys = gen.uniform_u64((1 << 22) + 99, bits, 5, 0 if bits == 64 else 2)
+    st = _u64_vs_oracle(cuda_lib, keys, key_bits=bits)
+    assert not st["fell_back_to_lsd"] and st["imbalance_max_over_mean"] < 2.0
+
+
+def test_learned_u64_skewed_and_keys_only(cuda_lib):
+    """u64 keys whose high half is lognormal and low half uniform, plus runs of
+    equal keys: narrow buckets split again on chip."""
+    n = 1 << 22
+    hi = gen.lognormal_u32(n, 20.0, 2.0, 14, 11).astype(np.uint64)
+    lo = gen.uniform_u32(n, 32, 14, 1).astype(np.uint64)
+    keys = (hi << np.uint64(32)) | lo
+    keys[: n // 8] = keys[7]
+    _u64_vs_oracle(cuda_lib, keys)
+    _u64_vs_oracle(cuda_lib, keys, vals=False)
+
+
+def test_learned_u64_full_size(cuda_lib):
+    """The 64-bit workload: 2^27 u64 keys uniform on [0, 2^64), payload = index."""
+    keys, vals = gen.workloads.wide_u64()
+    dk, dv = to_dev(keys), to_dev(vals)
+    st = cuda_lib.learned(dk, dv)
+    gk, gv = to_np(dk, np.uint64), to_np(dv, np.uint32)
+    del dk, dv
+    ek, ev = oracle.lsd(keys, vals, 0, 8)
+    assert np.array_equal(gk, ek) and np.array_equal(gv, ev)
+    assert not st["fell_back_to_lsd"]
+
+
 def test_learned_keys_only_and_key_bits(cuda_lib):
     keys = _keys("range20", (1 << 20) + 12345, seed=7)
     st = _learned_vs_oracle(cuda_lib, keys, vals=False, key_bits=20)
