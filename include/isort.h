@@ -163,8 +163,8 @@ ISORT_API isort_status isort_segmented(uint32_t* keys, uint32_t* vals, const uin
  *      (256 segments; knots X_0..X_256 and values Y_0..Y_256 are normalised
  *      cumulative sums of softplus(theta), so F is monotone by construction;
  *      knots start at the sample's quantiles) by 64 Adam steps on
- *      (1/m) sum_i (F(u_i) - (i + 1/2)/m)^2 over every 4th point of the
- *      sorted sample (m = 2^14), on the GPU;
+ *      (1/m) sum_i (F(u_i) - (i + 1/2)/m)^2 over every 8th point of the
+ *      sorted sample (m = 2^13), on the GPU;
  *   3. gives every key the bucket min(B - 1, floor(F(u) B)), F evaluated in a
  *      fixed fp32 order and clamped to each segment's value range, which makes
  *      the bucket monotone in the key (buckets are key ranges); the splitter
@@ -172,8 +172,8 @@ ISORT_API isort_status isort_segmented(uint32_t* keys, uint32_t* vals, const uin
  *   4. distributes the keys stably by bucket and sorts every bucket on chip on
  *      the bits its key range spans (a bucket of one key value is skipped).
  * The output is the stable sort of the input, whatever the model learned.
- * keys (u32), vals (optional) are device memory; nbuckets 2..16384 (0 = 4096,
- * doubled up to 16384 while n / nbuckets > 16,384; for u64 keys > 8,192);
+ * keys (u32), vals (optional) are device memory; nbuckets 2..32768 (0 = 4096,
+ * doubled up to 32768 while n / nbuckets > 16,384; for u64 keys > 8,192);
  * model 0 = the piecewise-linear CDF (1 = a small MLP: ISORT_ERR_UNSUPPORTED).
  * n < 2^18 sorts with the plain rounds. If more than half of the keys fall in
  * buckets beyond the on-chip capacity (65,536 keys) the call sorts with the

@@ -13,8 +13,8 @@
 //   1. sample m = 2^16 keys at indices drawn from SplitMix64 (Steele, Lea &
 //      Flood 2014), sort them with the library's own radix rounds;
 //   2. train the 256-segment PWL CDF (learned.cuh) by Adam on the mean squared
-//      error between F(u_i) and the empirical CDF (i + 1/2)/m of every 4th
-//      point of the sorted sample (m = 2^14, 64 points per segment); knot
+//      error between F(u_i) and the empirical CDF (i + 1/2)/m of every 8th
+//      point of the sorted sample (m = 2^13, 32 points per segment); knot
 //      positions start at sample quantiles, values at i/256; all steps run in
 //      one single-CTA kernel, and the parameters with the lowest loss seen
 //      (the initial ones included) are kept;
@@ -73,10 +73,10 @@ constexpr uint32_t kSampleSize = 1u << 16;
 constexpr uint64_t kSampleSeed = 0x5EED5EED5EEDull;
 constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
 constexpr int kTrainSteps = 64;
-constexpr uint32_t kFitStride = 4;  // the fit sees every 4th point of the sorted sample
+constexpr uint32_t kFitStride = 8;  // the fit sees every 8th point of the sorted sample
 constexpr float kLearningRate = 0.02f;
 constexpr uint32_t kOnChipCapacity = 65536;  // keys a cluster finishes on chip
-constexpr int kMaxBuckets = 16384;           // the splitter table is held in shared memory
+constexpr int kMaxBuckets = 32768;           // the census counts every bucket in shared memory
 
 __device__ __forceinline__ uint64_t splitmix_mix(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;

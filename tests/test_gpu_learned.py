@@ -160,7 +160,7 @@ def test_learned_rejects(cuda_lib):
     with pytest.raises(cuda_lib.IsortError, match="UNSUPPORTED|unsupported"):
         cuda_lib.learned(k, model=1)
     with pytest.raises(cuda_lib.IsortError):
-        cuda_lib.learned(k, nbuckets=32768)
+        cuda_lib.learned(k, nbuckets=65536)
     big = torch.full((1 << 19,), 1 << 21, dtype=torch.int32, device="cuda")
     with pytest.raises(cuda_lib.IsortError, match="RANGE|range"):
         cuda_lib.learned(big, key_bits=20)
