@@ -302,3 +302,16 @@ def test_full_size_range20(cuda_lib, rb):
     if rb == 11:
         rk, rv = oracle.lsd(keys, vals, 20, rb)
         assert np.array_equal(gk, rk) and np.array_equal(gv, rv)
+
+
+@pytest.mark.parametrize("bits", [64, 48])
+def test_full_size_u64(cuda_lib, bits):
+    """n = 2^27 u64 keys on [0, 2^bits) + payload (seed 5): 8 or 6 rounds at
+    radix 2^8, in place, bit-exact against the oracle."""
+    keys, vals = workloads.wide_u64(bits=bits)
+    ki, vi = to_dev(keys), to_dev(vals)
+    cuda_lib.radix(ki, vi, bits, 8)
+    gk, gv = to_np(ki, np.uint64), to_np(vi, np.uint32)
+    del ki, vi
+    ref_k, ref_v = oracle.lsd(keys, vals, bits, 8)
+    assert np.array_equal(gk, ref_k) and np.array_equal(gv, ref_v)
