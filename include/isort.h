@@ -262,6 +262,17 @@ ISORT_API isort_status isort_radix_noalloc(uint32_t* keys, uint32_t* vals, size_
  *   wait (look-back, copy completion). A wait that runs out records
  *   ISORT_ERR_TIMEOUT and the kernel returns. Default 2,000,000 (2 s).
  * ------------------------------------------------------------------------- */
+/* Autotuning of the count-sort rounds' launch shape (the library's own choice,
+ * not in the paper). enable = 1: the first radix sort of each kind (key width,
+ * payload or not, digits of <= 8 bits or wider, floor(log2 n); n >= 2^20)
+ * times the candidate shapes once on synthetic keys of the same size (it
+ * allocates scratch and synchronises the stream; not inside a stream capture)
+ * and keeps the fastest for the rest of the process; choices are read from
+ * cache_path (text, one "key_bytes payload wide log2n shape" per line; NULL:
+ * memory only) and appended to it. enable = 0: the built-in shapes.
+ * ISORT_ERR_INVALID_ARG for other values of enable. */
+ISORT_API isort_status isort_autotune(int enable, const char* cache_path);
+
 ISORT_API isort_status isort_set_sync(int on);
 ISORT_API isort_status isort_device_status(int clear, void* stream);
 ISORT_API isort_status isort_set_spin_limit(uint64_t microseconds);

@@ -75,6 +75,7 @@ SIGNATURES = [
     ("isort_cdf_loss_grad", _i32, [_vp, ctypes.c_uint32, _vp, _vp, _vp, _vp]),
     ("isort_cdf_splitters", _i32, [_vp, _vp, _i32, _i32, _i32, _vp, _vp]),
     ("isort_bucket_ids", _i32, [_vp, _i32, _sz, _i32, _vp, _vp, _i32, _vp, _vp]),
+    ("isort_autotune", _i32, [_i32, ctypes.c_char_p]),
     ("isort_set_sync", _i32, [_i32]),
     ("isort_device_status", _i32, [_i32, _vp]),
     ("isort_set_spin_limit", _i32, [_u64]),
@@ -299,6 +300,11 @@ def bucket_ids(keys, X, Y, nbuckets: int = 4096, key_bits: int = 0, stream=None)
     _check(load().isort_bucket_ids(_ptr(keys), w, keys.numel(), key_bits, _ptr(X), _ptr(Y), nbuckets, _ptr(ids),
                                    _stream(stream)), "isort_bucket_ids")
     return ids
+
+
+def autotune(enable: bool, cache_path: str | None = None):
+    """Turn the launch-shape autotuner on (with an optional cache file) or off."""
+    _check(load().isort_autotune(1 if enable else 0, cache_path.encode() if cache_path else None), "isort_autotune")
 
 
 def set_sync(on: bool):

@@ -19,6 +19,11 @@
 //                 digit in shared memory and write them out in runs.
 // So each round costs one read and one write of the keys (and payloads).
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -1012,14 +1017,17 @@ bool valid_widths(int key_width, int& key_bits, int rb) {
 
 // The same sort by chunked reduce-then-scan rounds (see k_downsweep).
 template <typename K>
+int autotuned_shape(const K* kin, bool vals, size_t n, int key_bits, int rb, cudaStream_t s);
+
+template <typename K>
 isort_status radix_device_rts(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n, int key_bits,
-                              int rb, cudaStream_t s) {
+                              int rb, cudaStream_t s, int shape = -1) {
     const int key_width = (int)sizeof(K) * 8;
     const int rounds = (key_bits + rb - 1) / rb;
     const int bins = 1 << rb;
     const bool vals = vin != nullptr;
     const bool inplace = (const void*)kin == (const void*)kout;
-    const int sh = bins <= 256 ? tune().sweep_small : tune().sweep_large;
+    const int sh = shape >= 0 ? shape : autotuned_shape<K>(kin, vals, n, key_bits, rb, s);
     int per_sm = 0;
     isort_status st = vals ? sweep_dispatch<K, true>(sh, true, bins, &per_sm, nullptr, 0, s)
                            : sweep_dispatch<K, false>(sh, true, bins, &per_sm, nullptr, 0, s);
@@ -1134,6 +1142,109 @@ isort_status radix_device_rts(const K* kin, const uint32_t* vin, K* kout, uint32
 
 // Sorts device buffers. kin/vin are read; the result lands in kout/vout.
 // If kin == kout the sort is in place (vin == vout then too).
+// ---------------------------------------------------------------- autotuning
+//
+// With autotuning on, the first chunked-round sort of each kind (key width,
+// payload or not, narrow or wide digits, log2 n; n >= 2^20) times the
+// candidate launch shapes once on synthetic keys of the same size and keeps
+// the fastest; choices are read from and appended to a cache file.
+struct AutoKey {
+    int key_bytes, vals, wide, log2n;
+    bool operator<(const AutoKey& o) const {
+        return std::tie(key_bytes, vals, wide, log2n) < std::tie(o.key_bytes, o.vals, o.wide, o.log2n);
+    }
+};
+
+struct AutoState {
+    std::mutex mu;
+    bool enabled = false;
+    std::string path;
+    std::map<AutoKey, int> shapes;
+};
+
+AutoState& auto_state() {
+    static AutoState st;
+    return st;
+}
+
+template <typename K>
+__global__ void k_fill_random(K* k, uint32_t* v, size_t n, uint64_t seed) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;  // SplitMix64 (Steele, Lea & Flood 2014)
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        k[i] = sizeof(K) == 4 ? (K)(z >> 32) : (K)z;
+        if (v) v[i] = (uint32_t)i;
+    }
+}
+
+template <typename K>
+int autotuned_shape(const K* kin, bool vals, size_t n, int key_bits, int rb, cudaStream_t s) {
+    (void)kin;
+    const int bins = 1 << rb;
+    const int fixed = bins <= 256 ? tune().sweep_small : tune().sweep_large;
+    AutoState& as = auto_state();
+    std::lock_guard<std::mutex> lk(as.mu);
+    if (!as.enabled || n < (size_t(1) << 20)) return fixed;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cap);
+    if (cap == cudaStreamCaptureStatusActive) return fixed;  // no timing inside a capture
+    int log2n = 0;
+    while ((size_t(1) << (log2n + 1)) <= n) ++log2n;
+    const AutoKey key{(int)sizeof(K), vals ? 1 : 0, bins > 256 ? 1 : 0, log2n};
+    const auto it = as.shapes.find(key);
+    if (it != as.shapes.end()) return it->second;
+
+    std::vector<int> cands = bins <= 256 ? std::vector<int>{4, 3, 1} : std::vector<int>{2, 0};
+    const size_t m = size_t(1) << log2n;
+    const size_t kb = align_up(m * sizeof(K), 256);
+    unsigned char* buf = nullptr;
+    if (scratch_alloc((void**)&buf, 2 * kb + (vals ? 2 * align_up(m * 4, 256) : 0), s) != ISORT_OK) return fixed;
+    K* k0 = reinterpret_cast<K*>(buf);
+    K* k1 = reinterpret_cast<K*>(buf + kb);
+    uint32_t* v0 = vals ? reinterpret_cast<uint32_t*>(buf + 2 * kb) : nullptr;
+    uint32_t* v1 = vals ? reinterpret_cast<uint32_t*>(buf + 2 * kb + align_up(m * 4, 256)) : nullptr;
+    k_fill_random<K><<<sm_count() * 4, 256, 0, s>>>(k0, v0, m, 0x5EEDull + (uint64_t)log2n);
+    int best = fixed;
+    float best_ms = 1e30f;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int c : cands) {
+        float ms = 0.f;
+        bool ok = true;
+        for (int rep = 0; rep < 3 && ok; ++rep) {  // one warm-up, two timed
+            cudaEventRecord(e0, s);
+            ok = radix_device_rts<K>(k0, v0, k1, v1, m, key_bits, rb, s, c) == ISORT_OK;
+            cudaEventRecord(e1, s);
+            if (ok && cudaEventSynchronize(e1) == cudaSuccess) {
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (rep > 0) ms += t;
+            } else {
+                ok = false;
+            }
+        }
+        if (ok && ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    scratch_free(buf, s);
+    cudaStreamSynchronize(s);
+    as.shapes[key] = best;
+    if (!as.path.empty()) {
+        if (FILE* f = std::fopen(as.path.c_str(), "a")) {
+            std::fprintf(f, "%d %d %d %d %d\n", key.key_bytes, key.vals, key.wide, key.log2n, best);
+            std::fclose(f);
+        }
+    }
+    return best;
+}
+
 template <typename K>
 isort_status radix_device(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n, int key_bits, int rb,
                           cudaStream_t s) {
@@ -1529,6 +1640,28 @@ isort_status isort_count_round(const uint32_t* keys_in, const uint32_t* vals_in,
 isort_status isort_count_round_u64(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
                                    uint32_t* vals_out, size_t n, int shift, int width, void* stream) {
     return count_round_entry<uint64_t>(keys_in, vals_in, keys_out, vals_out, n, shift, width, stream);
+}
+
+
+isort_status isort_autotune(int enable, const char* cache_path) {
+    if (enable != 0 && enable != 1) return ISORT_ERR_INVALID_ARG;
+    AutoState& as = auto_state();
+    std::lock_guard<std::mutex> lk(as.mu);
+    as.enabled = enable == 1;
+    as.shapes.clear();
+    as.path = cache_path ? cache_path : "";
+    if (as.enabled && cache_path) {
+        if (FILE* f = std::fopen(cache_path, "r")) {
+            AutoKey k;
+            int shape = 0;
+            while (std::fscanf(f, "%d %d %d %d %d", &k.key_bytes, &k.vals, &k.wide, &k.log2n, &shape) == 5) {
+                const int nshapes = (int)(sizeof(kSweepThreads) / sizeof(kSweepThreads[0]));
+                if (shape >= 0 && shape < nshapes) as.shapes[k] = shape;
+            }
+            std::fclose(f);
+        }
+    }
+    return ISORT_OK;
 }
 
 }  // extern "C"

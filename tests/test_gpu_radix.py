@@ -315,3 +315,23 @@ def test_full_size_u64(cuda_lib, bits):
     del ki, vi
     ref_k, ref_v = oracle.lsd(keys, vals, bits, 8)
     assert np.array_equal(gk, ref_k) and np.array_equal(gv, ref_v)
+
+
+def test_autotune_picks_a_shape_and_caches_it(cuda_lib, tmp_path):
+    """With autotuning on, the sort stays bit-exact, the choice is written to
+    the cache file, and a second process-level enable reads it back."""
+    path = str(tmp_path / "isort_tune.txt")
+    n = (1 << 21) + 3
+    keys = gen.uniform_u32(n, 32, 31, 0)
+    vals = np.arange(n, dtype=np.uint32)
+    try:
+        cuda_lib.autotune(True, path)
+        check(cuda_lib, keys, vals, 32, 8)
+        lines = open(path).read().split("\n")
+        rows = [list(map(int, ln.split())) for ln in lines if ln.strip()]
+        assert rows and rows[0][:4] == [4, 1, 0, 21]
+        cuda_lib.autotune(True, path)  # reads the cache: no new line for the same kind
+        check(cuda_lib, keys, vals, 32, 8)
+        assert len([ln for ln in open(path).read().split("\n") if ln.strip()]) == len(rows)
+    finally:
+        cuda_lib.autotune(False)
