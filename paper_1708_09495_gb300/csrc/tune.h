@@ -1,0 +1,21 @@
+// Tunables of the radix path (launch shapes and algorithm choices), shared by
+// the single-pass rounds (radix.cu) and the chunked rounds (rts.cu).
+#pragma once
+
+namespace isort {
+
+// Defaults are the measured best on GB300; the environment variable
+// ISORT_TUNE ("key=value,...") overrides them.
+struct Tune {
+    int hist_agg = 0;     // 1: match-any aggregation in the digit histogram
+    int rank_mode = 1;    // single-pass ranking: 1, per-bit ballots (the only one built)
+    int shape_small = 4;  // launch shape for digits of <= 8 bits
+    int shape_large = 1;  // launch shape for wider digits
+    int algo = 1;         // 0: single-pass rounds with look-back, 1: chunked reduce-then-scan rounds
+    int sweep_small = 4;  // chunked-round launch shape, digits of <= 8 bits (4: half-warp ranking)
+    int sweep_large = 2;  // chunked-round launch shape, wider digits
+};
+
+const Tune& tune();
+
+}  // namespace isort
