@@ -3,20 +3,23 @@
 // radix-r radix-sort", eq. Tp).
 //
 // The paper's round reads its input twice (count, then output) and writes it
-// once (3Ng per round). Here:
+// once (3Ng per round). The default rounds are the chunked reduce-then-scan
+// rounds (rts.cu, kernels in sweep.cuh: per-chunk counts, chunk offsets, rank
+// and scatter). This file holds the entry points and the single-pass rounds,
+// taken for digits whose per-tile tables do not fit the chunked round, by the
+// allocation-free entry point, and by the stalled-tile fault test:
 //   k_digit_hist  one streaming read of the keys (bulk copies into shared
-//                 memory, 128-bit shared loads, warp-aggregated shared atomics)
-//                 counts the digits of EVERY round at once, and ORs the keys for
-//                 the key-range check;
+//                 memory, 128-bit shared loads) counts the digits of EVERY
+//                 round at once, and ORs the keys for the key-range check;
 //   k_digit_scan  turns each round's counts into exclusive global offsets (the
 //                 paper's counts scatter/gather, 2rpg, becomes a table in HBM);
 //   k_onesweep    one launch per round: persistent CTAs take tiles in order,
 //                 prefetch the next tile with bulk copies, rank each key among
-//                 equal digits of its tile with match-any warp votes (input
-//                 order, so the round is stable), publish the tile's digit
-//                 counts and resolve the tile's global offsets with a
-//                 decoupled look-back over earlier tiles, then stage keys by
-//                 digit in shared memory and write them out in runs.
+//                 equal digits of its warp with one ballot per digit bit
+//                 (input order, so the round is stable), publish the tile's
+//                 digit counts and resolve the tile's global offsets with a
+//                 bounded decoupled look-back over earlier tiles, then stage
+//                 keys by digit in shared memory and write them out in runs.
 // So each round costs one read and one write of the keys (and payloads).
 #include <algorithm>
 #include <map>

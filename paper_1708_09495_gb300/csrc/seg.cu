@@ -75,7 +75,6 @@ struct SegThresholds {
 struct SegCtl {
     uint32_t status;
     uint32_t counts[kNumCls];
-    uint32_t work[kNumCls];
 };
 
 __global__ void k_seg_classify(const uint64_t* off, uint32_t nseg, SegThresholds th, SegCtl* ctl, uint32_t* lists,
