@@ -71,9 +71,13 @@ ISORT_API const char* isort_status_string(isort_status s);
 /* ---------------------------------------------------------------------------
  * LSD radix sort (Section 3, "Serial/Parallel radix-r radix-sort", eqs. Ts, Tp:
  * ceil(key_bits / lg r) rounds of count-sort, least significant digit first).
- * One read of the keys builds the digit counts of every round; each round then
- * reads and writes the keys (and payloads) once, ranking keys inside a tile and
- * resolving tile offsets with a decoupled look-back prefix.
+ * Each round counts the digits of contiguous chunks of the keys (one read),
+ * turns the counts into every chunk's output offsets (the paper's exchange of
+ * counts between processors), and ranks and scatters the keys (and payloads)
+ * chunk by chunk (one read, one write). Digits wider than the chunked round's
+ * tables take single-pass rounds (all rounds' counts from one read, tile
+ * offsets by a bounded decoupled look-back). radix_bits above 12 returns
+ * ISORT_ERR_UNSUPPORTED.
  * In place: on ISORT_OK keys (and vals) hold the sorted result.
  * ------------------------------------------------------------------------- */
 ISORT_API isort_status isort_radix(uint32_t* keys, uint32_t* vals, size_t n, int key_bits, int radix_bits, void* stream);
