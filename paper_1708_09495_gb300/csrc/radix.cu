@@ -1025,6 +1025,51 @@ isort_status radix_device(const K* kin, const uint32_t* vin, K* kout, uint32_t* 
 }
 
 // Entry: validates, stages host buffers through device memory if needed.
+// A copy ordered on `s`, cut into up to kCopyStreams pieces of at least 64 MiB
+// that run on the calling thread's auxiliary streams for this device.
+constexpr int kCopyStreams = 4;
+
+struct CopyStreams {
+    int device = -1;
+    cudaStream_t st[kCopyStreams] = {};
+    cudaEvent_t ev[kCopyStreams + 1] = {};
+};
+
+thread_local CopyStreams t_copy;
+
+cudaError_t copy_split(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return ce;
+    CopyStreams& cs = t_copy;
+    if (cs.device != dev) {  // created once per thread and device, kept for the process
+        for (int i = 0; i < kCopyStreams; ++i) {
+            if (cudaStreamCreateWithFlags(&cs.st[i], cudaStreamNonBlocking) != cudaSuccess) return cudaGetLastError();
+        }
+        for (int i = 0; i <= kCopyStreams; ++i) {
+            if (cudaEventCreateWithFlags(&cs.ev[i], cudaEventDisableTiming) != cudaSuccess) return cudaGetLastError();
+        }
+        cs.device = dev;
+    }
+    const size_t piece_min = size_t(64) << 20;
+    const int pieces = (int)std::min<size_t>(kCopyStreams, std::max<size_t>(1, bytes / piece_min));
+    if (pieces <= 1) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s);
+    ce = cudaEventRecord(cs.ev[kCopyStreams], s);  // the copies start after the work before them
+    const size_t step = align_up((bytes + pieces - 1) / pieces, 4096);
+    for (int i = 0; i < pieces && ce == cudaSuccess; ++i) {
+        const size_t off = (size_t)i * step;
+        if (off >= bytes) break;
+        const size_t len = std::min(step, bytes - off);
+        ce = cudaStreamWaitEvent(cs.st[i], cs.ev[kCopyStreams], 0);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync(static_cast<char*>(dst) + off, static_cast<const char*>(src) + off, len,
+                                 cudaMemcpyDefault, cs.st[i]);
+        if (ce == cudaSuccess) ce = cudaEventRecord(cs.ev[i], cs.st[i]);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s, cs.ev[i], 0);  // the work after them waits
+    }
+    return ce;
+}
+
 template <typename K>
 isort_status radix_entry(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n, int key_bits, int rb,
                          void* stream) {
@@ -1048,15 +1093,17 @@ isort_status radix_entry(const K* kin, const uint32_t* vin, K* kout, uint32_t* v
     const bool host = is_host_pointer(kin) || is_host_pointer(kout) || (vin && (is_host_pointer(vin) || is_host_pointer(vout)));
     if (!host) return radix_device<K>(kin, vin, kout, vout, n, key_bits, rb, s);
 
-    // Host buffers: copy in, sort in place on the device, copy out.
+    // Host buffers: copy in, sort in place on the device, copy out. The copies
+    // are cut into pieces spread over a few streams (several DMA transfers at
+    // once), joined to `s` by events.
     const size_t kb = align_up(n * sizeof(K), 256);
     unsigned char* st_buf = nullptr;
     isort_status st = scratch_alloc((void**)&st_buf, kb + (vin ? align_up(n * 4, 256) : 0), s);
     if (st != ISORT_OK) return st;
     K* dk = reinterpret_cast<K*>(st_buf);
     uint32_t* dv = vin ? reinterpret_cast<uint32_t*>(st_buf + kb) : nullptr;
-    cudaError_t ce = cudaMemcpyAsync(dk, kin, n * sizeof(K), cudaMemcpyDefault, s);
-    if (ce == cudaSuccess && vin) ce = cudaMemcpyAsync(dv, vin, n * 4, cudaMemcpyDefault, s);
+    cudaError_t ce = copy_split(dk, kin, n * sizeof(K), s);
+    if (ce == cudaSuccess && vin) ce = copy_split(dv, vin, n * 4, s);
     if (ce != cudaSuccess) {
         scratch_free(st_buf, s);
         return from_cuda(ce);
@@ -1065,8 +1112,8 @@ isort_status radix_entry(const K* kin, const uint32_t* vin, K* kout, uint32_t* v
     st = radix_device<K>(dk, dv, dk, dv, n, key_bits, rb, s);
     if (st == ISORT_OK || st == ISORT_ERR_TIMEOUT) {
         if (st == ISORT_OK) {
-            ce = cudaMemcpyAsync(kout, dk, n * sizeof(K), cudaMemcpyDefault, s);
-            if (ce == cudaSuccess && vin) ce = cudaMemcpyAsync(vout, dv, n * 4, cudaMemcpyDefault, s);
+            ce = copy_split(kout, dk, n * sizeof(K), s);
+            if (ce == cudaSuccess && vin) ce = copy_split(vout, dv, n * 4, s);
             if (ce != cudaSuccess) st = from_cuda(ce);
         }
     }

@@ -151,6 +151,28 @@ def test_host_buffers(cuda_lib):
     assert np.array_equal(ko, rk) and np.array_equal(vo, rv)
 
 
+def test_host_buffers_large_split_copies(cuda_lib):
+    """Host buffers large enough for the staging copies to be cut into pieces
+    on several streams: pinned (torch) and pageable (numpy), in place and out."""
+    import torch
+
+    lib = cuda_lib.load()
+    n = (1 << 25) + 7
+    keys = gen.uniform_u32(n, 32, 14, 0)
+    vals = np.arange(n, dtype=np.uint32)
+    rk, rv = oracle.lsd(keys, vals, 32, 8)
+    hk = torch.from_numpy(keys.view(np.int32).copy()).pin_memory()
+    hv = torch.from_numpy(vals.view(np.int32).copy()).pin_memory()
+    rc = lib.isort_radix(ctypes.c_void_p(hk.data_ptr()), ctypes.c_void_p(hv.data_ptr()), n, 32, 8, None)
+    assert rc == 0
+    assert np.array_equal(hk.numpy().view(np.uint32), rk) and np.array_equal(hv.numpy().view(np.uint32), rv)
+    ko, vo = np.empty_like(keys), np.empty_like(vals)
+    rc = lib.isort_radix_copy(keys.ctypes.data_as(ctypes.c_void_p), vals.ctypes.data_as(ctypes.c_void_p),
+                              ko.ctypes.data_as(ctypes.c_void_p), vo.ctypes.data_as(ctypes.c_void_p), n, 32, 8, None)
+    assert rc == 0
+    assert np.array_equal(ko, rk) and np.array_equal(vo, rv)
+
+
 def test_key_range_violation_leaves_buffers(cuda_lib):
     import torch
 
