@@ -79,6 +79,10 @@ def _lib(mutant: int = 0):
             h.oracle_cdf_knots.restype = None
             h.oracle_cdf_loss_grad.argtypes = [vp, ctypes.c_uint32, vp, vp]
             h.oracle_cdf_loss_grad.restype = ctypes.c_double
+            h.oracle_mlp_cdf.argtypes = [vp, ctypes.c_double]
+            h.oracle_mlp_cdf.restype = ctypes.c_double
+            h.oracle_mlp_loss_grad.argtypes = [vp, ctypes.c_uint32, vp, vp]
+            h.oracle_mlp_loss_grad.restype = ctypes.c_double
             _handles[mutant] = h
     return h
 
@@ -255,4 +259,23 @@ def cdf_loss_grad(u, theta, with_grad: bool = True):
     t = np.ascontiguousarray(theta, dtype=np.float64)
     g = np.zeros(512, np.float64) if with_grad else None
     loss = _lib().oracle_cdf_loss_grad(_p(uu), uu.size, _p(t), _p(g))
+    return float(loss), g
+
+
+MLP_HIDDEN = 32
+MLP_PARAMS = 3 * MLP_HIDDEN + 1
+
+
+def mlp_cdf(params, u: float) -> float:
+    """F(u) of the 1-32-1 monotone MLP model (double)."""
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    return float(_lib().oracle_mlp_cdf(_p(p), float(u)))
+
+
+def mlp_loss_grad(u, params, with_grad: bool = True):
+    """(loss, dloss/dparams) of the MLP model in double precision."""
+    uu = np.ascontiguousarray(u, dtype=np.float64)
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    g = np.zeros(MLP_PARAMS, np.float64) if with_grad else None
+    loss = _lib().oracle_mlp_loss_grad(_p(uu), uu.size, _p(p), _p(g))
     return float(loss), g

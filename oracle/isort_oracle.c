@@ -518,3 +518,85 @@ double oracle_cdf_loss_grad(const double* u, uint32_t m, const double* theta, do
     }
     return loss;
 }
+
+/* ---- The alternative model: a 1-32-1 monotone MLP CDF, in double.
+ * Parameters p[0..31] = a1 (W1_j = softplus(a1_j)), p[32..63] = b1,
+ * p[64..95] = a2 (W2_j = softplus(a2_j)), p[96] = b2, sigmoid hidden units:
+ *   z(u) = sum_j W2_j sigma(W1_j u + b1_j) + b2,
+ *   F(u) = (z(u) - z(0)) / (z(1) - z(0)).
+ * Positive weights and an increasing sigma make F increasing, with F(0) = 0 and
+ * F(1) = 1 (b2 cancels). Loss as for the PWL model. */
+#define MLP_H 32
+#define MLP_P (3 * MLP_H + 1)
+
+static double sigmoid_d(double x) { return 1.0 / (1.0 + exp(-x)); }
+
+static double mlp_z(const double* p, double u) {
+    double z = p[3 * MLP_H];
+    for (int j = 0; j < MLP_H; ++j) z += softplus_d(p[2 * MLP_H + j]) * sigmoid_d(softplus_d(p[j]) * u + p[MLP_H + j]);
+    return z;
+}
+
+double oracle_mlp_cdf(const double* p, double u) {
+    double z0 = mlp_z(p, 0.0), z1 = mlp_z(p, 1.0);
+    return (mlp_z(p, u) - z0) / (z1 - z0);
+}
+
+/* d z(u) / d(W1_j, b1_j, W2_j) for every j */
+static void mlp_dz(const double* p, double u, double* dW1, double* db1, double* dW2) {
+    for (int j = 0; j < MLP_H; ++j) {
+        double w1 = softplus_d(p[j]), w2 = softplus_d(p[2 * MLP_H + j]);
+        double h = sigmoid_d(w1 * u + p[MLP_H + j]);
+        double s = w2 * h * (1.0 - h);
+        dW1[j] = s * u;
+        db1[j] = s;
+        dW2[j] = h;
+    }
+}
+
+/* Loss (1/m) sum_i (F(u_i) - (i + 1/2)/m)^2 and its gradient with respect to
+ * p (grad may be NULL), by the chain rule through the normalisation:
+ * dF/dz(u) = 1/D, dF/dz(0) = (F - 1)/D, dF/dz(1) = -F/D, D = z(1) - z(0);
+ * then through softplus for a1 and a2. */
+double oracle_mlp_loss_grad(const double* u, uint32_t m, const double* p, double* grad) {
+    double z0 = mlp_z(p, 0.0), z1 = mlp_z(p, 1.0), D = z1 - z0;
+    double gW1[MLP_H] = {0}, gb1[MLP_H] = {0}, gW2[MLP_H] = {0};
+    double dW1[MLP_H], db1[MLP_H], dW2[MLP_H];
+    double c0 = 0.0, c1 = 0.0, loss = 0.0;
+    for (uint32_t i = 0; i < m; ++i) {
+        double F = (mlp_z(p, u[i]) - z0) / D;
+        double e = F - ((double)i + 0.5) / m;
+        loss += e * e / m;
+        if (!grad) continue;
+        double g = 2.0 * e / m;
+        mlp_dz(p, u[i], dW1, db1, dW2);
+        for (int j = 0; j < MLP_H; ++j) {
+            gW1[j] += g / D * dW1[j];
+            gb1[j] += g / D * db1[j];
+            gW2[j] += g / D * dW2[j];
+        }
+        c0 += g * (F - 1.0) / D;
+        c1 += -g * F / D;
+    }
+    if (grad) {
+        mlp_dz(p, 0.0, dW1, db1, dW2);
+        for (int j = 0; j < MLP_H; ++j) {
+            gW1[j] += c0 * dW1[j];
+            gb1[j] += c0 * db1[j];
+            gW2[j] += c0 * dW2[j];
+        }
+        mlp_dz(p, 1.0, dW1, db1, dW2);
+        for (int j = 0; j < MLP_H; ++j) {
+            gW1[j] += c1 * dW1[j];
+            gb1[j] += c1 * db1[j];
+            gW2[j] += c1 * dW2[j];
+        }
+        for (int j = 0; j < MLP_H; ++j) {
+            grad[j] = gW1[j] / (1.0 + exp(-p[j]));
+            grad[MLP_H + j] = gb1[j];
+            grad[2 * MLP_H + j] = gW2[j] / (1.0 + exp(-p[2 * MLP_H + j]));
+        }
+        grad[3 * MLP_H] = 0.0; /* b2 cancels in F */
+    }
+    return loss;
+}
