@@ -25,6 +25,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+MODELS = {0: "piecewise-linear CDF", 1: "1-32-1 MLP CDF"}
 METRIC = "Gkeys/s (u32 n=2^28) & % HBM roofline; learned/batched vs plain LSD, bit-exact"
 UNIT = "Gkeys/s"
 N = 1 << 28
@@ -438,7 +439,7 @@ def run_compare(args):
 
         def learned():
             rc = lib.isort_learned_u64(ctypes.c_void_p(kw.data_ptr()), ctypes.c_void_p(vw.data_ptr()), n, bits,
-                                       args.nbuckets, 0, ctypes.byref(st), sp)
+                                       args.nbuckets, args.model, ctypes.byref(st), sp)
             if rc != 0:
                 raise RuntimeError(f"isort_learned_u64: {isort.STATUS.get(rc, rc)}")
 
@@ -462,8 +463,8 @@ def run_compare(args):
         ms_p = _timed_inplace(plain, reset, args.steps, args.warmup, stream)
         line.update({
             "value": args.steps * n / (ms_l * 1e-3) / 1e9, "ms_per_step": ms_l / args.steps, "dtype": "u64",
-            "config": {"workload": f"learned-bucket sort, u64 keys uniform on [0,2^{bits}) (seed 5) + u32 payload "
-                                   f"= index, n = 2^27", "l2": "inputs larger than L2; restored before each step "
+            "config": {"workload": f"learned-bucket sort ({MODELS[args.model]}), u64 keys uniform on [0,2^{bits}) "
+                                   f"(seed 5) + u32 payload = index, n = 2^27", "l2": "inputs larger than L2; restored before each step "
                                                                "(untimed)"},
             "plain_lsd": {"value": args.steps * n / (ms_p * 1e-3) / 1e9, "ms_per_step": ms_p / args.steps,
                           "call": f"isort_radix_u64, radix 2^8, {bits // 8} rounds, in place"},
@@ -479,7 +480,8 @@ def run_compare(args):
         st = isort.LearnedStats()
 
         def learned():
-            rc = lib.isort_learned(ctypes.c_void_p(kw.data_ptr()), None, n, 32, args.nbuckets, 0, ctypes.byref(st), sp)
+            rc = lib.isort_learned(ctypes.c_void_p(kw.data_ptr()), None, n, 32, args.nbuckets, args.model,
+                                   ctypes.byref(st), sp)
             if rc != 0:
                 raise RuntimeError(f"isort_learned: {isort.STATUS.get(rc, rc)}")
 
@@ -504,7 +506,8 @@ def run_compare(args):
         achieved = n * 8 / (sw[1] / sw[0] * 1e-3) / 1e9 if sw[0] else None
         line.update({
             "value": value, "ms_per_step": ms_l / args.steps,
-            "config": {"workload": f"learned-bucket sort, u32 keys-only, {args.dist} (seed 6), n = 2^{args.log2n}",
+            "config": {"workload": f"learned-bucket sort ({MODELS[args.model]}), u32 keys-only, {args.dist} (seed 6), "
+                                   f"n = 2^{args.log2n}",
                        "l2": "inputs larger than L2; restored before each step (untimed)"},
             "plain_lsd": {"value": args.steps * n / (ms_p * 1e-3) / 1e9, "ms_per_step": ms_p / args.steps,
                           "call": "isort_radix, radix 2^8, in place"},
@@ -584,6 +587,8 @@ def main():
                     help="uniform: the benchmark; learned / segmented: secondary comparisons with plain LSD; "
                          "small: the 65,536-key case and the block networks on 1,024 keys")
     ap.add_argument("--nbuckets", type=int, default=0, help="learned: bucket count (0: the library's choice)")
+    ap.add_argument("--model", type=int, default=0, choices=[0, 1],
+                    help="learned: 0 = piecewise-linear CDF, 1 = the 1-32-1 MLP CDF")
     ap.add_argument("--dist", default="lognormal", choices=["zipf", "lognormal", "gmm", "range48"],
                     help="learned: key distribution; learned64: range48 for keys on [0, 2^48)")
     args = ap.parse_args()

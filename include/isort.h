@@ -178,7 +178,9 @@ ISORT_API isort_status isort_segmented(uint32_t* keys, uint32_t* vals, const uin
  * The output is the stable sort of the input, whatever the model learned.
  * keys (u32), vals (optional) are device memory; nbuckets 2..32768 (0 = 4096,
  * doubled up to 32768 while n / nbuckets > 16,384; for u64 keys > 8,192);
- * model 0 = the piecewise-linear CDF (1 = a small MLP: ISORT_ERR_UNSUPPORTED).
+ * model 0 = the piecewise-linear CDF of step 2; model 1 = a 1-32-1 monotone
+ * MLP CDF instead (see isort_mlp_train), trained on every 16th point of the
+ * sorted sample and tabulated as the 257 knots (X_k, Y_k) steps 3-4 read.
  * n < 2^18 sorts with the plain rounds. If more than half of the keys fall in
  * buckets beyond the on-chip capacity (65,536 keys) the call sorts with the
  * plain rounds instead (stats->fell_back_to_lsd = 1); fewer such buckets are
@@ -229,6 +231,29 @@ ISORT_API isort_status isort_cdf_splitters(const float* X, const float* Y, int k
                                            void* splitters, void* stream);
 ISORT_API isort_status isort_bucket_ids(const void* keys, int key_width, size_t n, int key_bits, const float* X,
                                         const float* Y, int nbuckets, uint32_t* ids, void* stream);
+
+/* The MLP model (isort_learned with model = 1). Parameters (device, 97
+ * floats): a1[32], b1[32], a2[32], b2, with W1 = softplus(a1),
+ * W2 = softplus(a2),
+ *   z(u) = sum_j W2_j sigmoid(W1_j u + b1_j) + b2,
+ *   F(u) = (z(u) - z(0)) / (z(1) - z(0)),
+ * increasing with F(0) = 0, F(1) = 1 (b2 cancels). Same loss as step 2.
+ * isort_mlp_train: from a sorted sample (device, m u32 keys) sets the initial
+ *   parameters (unit j centred at the sample's (j + 1/2)/32 quantile, rising
+ *   over its quantile interval; W2 = 1/32), runs 64 Adam steps on one
+ *   cluster of 8 CTAs over all m points, and writes params (the lowest loss
+ *   seen), X, Y (device, 257 each: X_0 = 0, X_k = the normalised key of rank
+ *   k m / 256, X_256 = 1; Y_k = F(X_k) clamped to [0, 1] and made
+ *   non-decreasing, Y_0 = 0, Y_256 = 1) and losses (device, 66 floats, laid
+ *   out as for isort_cdf_train).
+ * isort_mlp_loss_grad: loss and d loss / d params at params (device, 97) on
+ *   u (device, m normalised sorted values); grad (device, 97; the b2 entry is
+ *   0) and loss (device, 1) receive them.
+ */
+ISORT_API isort_status isort_mlp_train(const uint32_t* sorted_sample, uint32_t m, int key_bits, float* params, float* X,
+                                       float* Y, float* losses, void* stream);
+ISORT_API isort_status isort_mlp_loss_grad(const float* u, uint32_t m, const float* params, float* grad, float* loss,
+                                           void* stream);
 
 /* ---------------------------------------------------------------------------
  * isort_radix_noalloc: isort_radix (in place, u32 keys, optional u32 payload)

@@ -73,6 +73,8 @@ SIGNATURES = [
     ("isort_learned_u64", _i32, [_vp, _vp, _sz, _i32, _i32, _i32, _vp, _vp]),
     ("isort_cdf_train", _i32, [_vp, ctypes.c_uint32, _i32, _vp, _vp, _vp, _vp, _vp]),
     ("isort_cdf_loss_grad", _i32, [_vp, ctypes.c_uint32, _vp, _vp, _vp, _vp]),
+    ("isort_mlp_train", _i32, [_vp, ctypes.c_uint32, _i32, _vp, _vp, _vp, _vp, _vp]),
+    ("isort_mlp_loss_grad", _i32, [_vp, ctypes.c_uint32, _vp, _vp, _vp, _vp]),
     ("isort_cdf_splitters", _i32, [_vp, _vp, _i32, _i32, _i32, _vp, _vp]),
     ("isort_bucket_ids", _i32, [_vp, _i32, _sz, _i32, _vp, _vp, _i32, _vp, _vp]),
     ("isort_autotune", _i32, [_i32, ctypes.c_char_p]),
@@ -248,7 +250,8 @@ def segmented(keys, vals, offsets, key_bits: int = 0, stream=None):
 
 def learned(keys, vals=None, key_bits: int = 0, nbuckets: int = 0, model: int = 0, stream=None):
     """Learned-bucket stable sort of uint32 or uint64 keys (in place). Returns
-    the stats dict. nbuckets 0 lets the library choose (4096 up to 16384 with n)."""
+    the stats dict. nbuckets 0 lets the library choose (4096 up to 32768 with n);
+    model 0 = the piecewise-linear CDF, 1 = the MLP CDF."""
     st = LearnedStats()
     fn = load().isort_learned if _key_width(keys) == 32 else load().isort_learned_u64
     _check(fn(_ptr(keys), _ptr(vals), keys.numel(), key_bits, nbuckets, model, ctypes.byref(st), _stream(stream)),
@@ -278,6 +281,31 @@ def cdf_loss_grad(u, theta, stream=None):
     loss = torch.empty(1, dtype=torch.float32, device=u.device)
     _check(load().isort_cdf_loss_grad(_ptr(u), u.numel(), _ptr(theta), _ptr(grad), _ptr(loss), _stream(stream)),
            "isort_cdf_loss_grad")
+    return loss, grad
+
+
+def mlp_train(sorted_sample, key_bits: int = 32, stream=None):
+    """Trains the MLP CDF model on a sorted uint32 sample; returns (params, X, Y, losses) tensors."""
+    import torch
+
+    dev = sorted_sample.device
+    params = torch.empty(97, dtype=torch.float32, device=dev)
+    X = torch.empty(257, dtype=torch.float32, device=dev)
+    Y = torch.empty(257, dtype=torch.float32, device=dev)
+    losses = torch.empty(66, dtype=torch.float32, device=dev)
+    _check(load().isort_mlp_train(_ptr(sorted_sample), sorted_sample.numel(), key_bits, _ptr(params), _ptr(X), _ptr(Y),
+                                  _ptr(losses), _stream(stream)), "isort_mlp_train")
+    return params, X, Y, losses
+
+
+def mlp_loss_grad(u, params, stream=None):
+    """(loss, grad) of the MLP CDF model at params on normalised sorted sample values u."""
+    import torch
+
+    grad = torch.empty(97, dtype=torch.float32, device=u.device)
+    loss = torch.empty(1, dtype=torch.float32, device=u.device)
+    _check(load().isort_mlp_loss_grad(_ptr(u), u.numel(), _ptr(params), _ptr(grad), _ptr(loss), _stream(stream)),
+           "isort_mlp_loss_grad")
     return loss, grad
 
 

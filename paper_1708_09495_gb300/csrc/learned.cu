@@ -50,6 +50,14 @@ isort_status segmented_finish_u64(uint64_t* keys, uint32_t* vals, const uint64_t
                                   const uint64_t* seg_lo, const uint8_t* seg_bits, cudaStream_t s);
 isort_status segmented_finish_u32(uint32_t* keys, uint32_t* vals, const uint64_t* off, uint32_t nseg,
                                   const uint32_t* seg_lo, const uint8_t* seg_bits, cudaStream_t s);
+// The MLP model of a sorted sample, tabulated as X, Y (mlp.cu).
+template <typename K>
+isort_status mlp_model(const K* sorted, uint32_t m, float scale, float* u, float* params, float* X, float* Y,
+                       float* losses, cudaStream_t s);
+extern template isort_status mlp_model<uint32_t>(const uint32_t*, uint32_t, float, float*, float*, float*, float*,
+                                                 float*, cudaStream_t);
+extern template isort_status mlp_model<uint64_t>(const uint64_t*, uint32_t, float, float*, float*, float*, float*,
+                                                 float*, cudaStream_t);
 
 namespace {
 
@@ -72,7 +80,6 @@ isort_status finish_buckets(uint64_t* k, uint32_t* v, const uint64_t* off, uint3
 constexpr uint32_t kSampleSize = 1u << 16;
 constexpr uint64_t kSampleSeed = 0x5EED5EED5EEDull;
 constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
-constexpr int kTrainSteps = 64;
 constexpr uint32_t kFitStride = 8;  // the fit sees every 8th point of the sorted sample
 constexpr float kLearningRate = 0.02f;
 constexpr uint32_t kOnChipCapacity = 65536;  // keys a cluster finishes on chip
@@ -602,8 +609,8 @@ isort_status launch_bucket_sweep(const SweepArgs& a, const BucketDigit<K>& df, u
 }
 
 template <typename K>
-isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int B, isort_learned_stats* stats,
-                            cudaStream_t s) {
+isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int B, int model,
+                            isort_learned_stats* stats, cudaStream_t s) {
     std::memset(stats, 0, sizeof(*stats));
     const float scale = std::ldexp(1.0f, -key_bits);
     const uint32_t m = kSampleSize;
@@ -639,7 +646,7 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
     };
     const size_t o_status = take(64);
     const size_t o_sample = take((size_t)m * sizeof(K)), o_u = take((size_t)m * 4);
-    const size_t o_theta = take(2 * kPwlSegments * 4);
+    const size_t o_theta = take(2 * kPwlSegments * 4);  // also holds the MLP's 97 parameters
     const size_t o_X = take(kPwlKnots * 4), o_Y = take(kPwlKnots * 4);
     const size_t o_loss = take((kTrainSteps + 2) * 4);
     const size_t o_split = take((size_t)B * sizeof(K)), o_bcount = take((size_t)B * 4);
@@ -685,15 +692,19 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
     st = plain_sort(sample, nullptr, m, key_bits, s);
     if (st != ISORT_OK) return fail(st);
 
-    // 2. train the model
-    {
-        LaunchScope ls("cdf_init", s);
-        k_normalise<K><<<(m / kFitStride + 255) / 256, 256, 0, s>>>(sample, m / kFitStride, kFitStride, scale, u);
-        k_model_init<K><<<1, kPwlSegments, 0, s>>>(sample, m, scale, theta);
-        ce = cudaGetLastError();
-        if (ce != cudaSuccess) return fail(from_cuda(ce));
+    // 2. train the model (both leave their CDF as the table X, Y)
+    if (model == 0) {
+        {
+            LaunchScope ls("cdf_init", s);
+            k_normalise<K><<<(m / kFitStride + 255) / 256, 256, 0, s>>>(sample, m / kFitStride, kFitStride, scale, u);
+            k_model_init<K><<<1, kPwlSegments, 0, s>>>(sample, m, scale, theta);
+            ce = cudaGetLastError();
+            if (ce != cudaSuccess) return fail(from_cuda(ce));
+        }
+        st = launch_fit(u, m / kFitStride, theta, X, Y, losses, nullptr, nullptr, kTrainSteps, s);
+    } else {
+        st = mlp_model<K>(sample, m, scale, u, theta, X, Y, losses, s);
     }
-    st = launch_fit(u, m / kFitStride, theta, X, Y, losses, nullptr, nullptr, kTrainSteps, s);
     if (st != ISORT_OK) return fail(st);
 
     // 3. splitters
@@ -874,7 +885,6 @@ isort_status learned_entry(K* keys, uint32_t* vals, size_t n, int key_bits, int 
     }
     if (nbuckets < 2 || nbuckets > kMaxBuckets) return ISORT_ERR_INVALID_ARG;
     if (model != 0 && model != 1) return ISORT_ERR_INVALID_ARG;
-    if (model == 1) return ISORT_ERR_UNSUPPORTED;
     if (n >= (size_t(1) << 30)) return ISORT_ERR_UNSUPPORTED;
     if (n > 1 && !keys) return ISORT_ERR_INVALID_ARG;
     if (n <= 1) return ISORT_OK;
@@ -885,7 +895,7 @@ isort_status learned_entry(K* keys, uint32_t* vals, size_t n, int key_bits, int 
         st->fell_back_to_lsd = 1;
         return plain_sort(keys, vals, n, key_bits, s);
     }
-    return learned_device<K>(keys, vals, n, key_bits, nbuckets, st, s);
+    return learned_device<K>(keys, vals, n, key_bits, nbuckets, model, st, s);
 }
 
 }  // namespace

@@ -19,6 +19,7 @@ namespace isort {
 
 constexpr int kPwlSegments = 256;
 constexpr int kPwlKnots = kPwlSegments + 1;
+constexpr int kTrainSteps = 64;  // Adam steps of either model's fit
 
 template <typename K>
 __device__ __forceinline__ float normalise_key(K k, float scale) {

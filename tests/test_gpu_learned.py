@@ -157,8 +157,8 @@ def test_learned_rejects(cuda_lib):
     import torch
 
     k = torch.zeros(1 << 19, dtype=torch.int32, device="cuda")
-    with pytest.raises(cuda_lib.IsortError, match="UNSUPPORTED|unsupported"):
-        cuda_lib.learned(k, model=1)
+    with pytest.raises(cuda_lib.IsortError, match="INVALID|invalid"):
+        cuda_lib.learned(k, model=2)
     with pytest.raises(cuda_lib.IsortError):
         cuda_lib.learned(k, nbuckets=65536)
     big = torch.full((1 << 19,), 1 << 21, dtype=torch.int32, device="cuda")
