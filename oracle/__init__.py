@@ -79,6 +79,8 @@ def _lib(mutant: int = 0):
             h.oracle_cdf_knots.restype = None
             h.oracle_cdf_loss_grad.argtypes = [vp, ctypes.c_uint32, vp, vp]
             h.oracle_cdf_loss_grad.restype = ctypes.c_double
+            h.oracle_sort_typed.argtypes = [vp, i32, vp, sz]
+            h.oracle_sort_typed.restype = i32
             h.oracle_mlp_cdf.argtypes = [vp, ctypes.c_double]
             h.oracle_mlp_cdf.restype = ctypes.c_double
             h.oracle_mlp_loss_grad.argtypes = [vp, ctypes.c_uint32, vp, vp]
@@ -279,3 +281,20 @@ def mlp_loss_grad(u, params, with_grad: bool = True):
     g = np.zeros(MLP_PARAMS, np.float64) if with_grad else None
     loss = _lib().oracle_mlp_loss_grad(_p(uu), uu.size, _p(p), _p(g))
     return float(loss), g
+
+
+KEY_TYPES = {"i32": (1, np.int32), "f32": (2, np.float32), "i64": (4, np.int64), "f64": (5, np.float64)}
+
+
+def sort_typed(keys, vals=None):
+    """Stable sort of int32/float32/int64/float64 keys by the order of their
+    type (floats: IEEE 754 totalOrder, on the bits); returns (keys, vals)."""
+    name = {np.dtype(t): n for n, (_, t) in KEY_TYPES.items()}.get(np.asarray(keys).dtype)
+    if name is None:
+        raise TypeError(f"keys must be int32, float32, int64 or float64, got {np.asarray(keys).dtype}")
+    k = np.array(keys, copy=True)
+    v = None if vals is None else np.ascontiguousarray(vals, dtype=np.uint32).copy()
+    rc = _lib().oracle_sort_typed(_p(k), KEY_TYPES[name][0], _p(v), k.size)
+    if rc != 0:
+        raise RuntimeError(f"oracle_sort_typed failed ({rc})")
+    return k, v

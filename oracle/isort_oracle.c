@@ -600,3 +600,70 @@ double oracle_mlp_loss_grad(const double* u, uint32_t m, const double* p, double
     }
     return loss;
 }
+
+/* ---- Typed keys: signed integers and IEEE 754 floats, sorted stably by the
+ * order of their type (the paper sorts unsigned integers from a known range;
+ * signed and floating-point keys are the usual extension). The order is
+ * written out as a comparison on the key's bits:
+ *   signed integers (two's complement): by value;
+ *   floats (binary32, binary64): IEEE 754 totalOrder: keys with the sign bit
+ *   set come first, ordered by decreasing magnitude bits (all bits but the
+ *   sign); then keys with the sign bit clear, by increasing magnitude bits.
+ *   So -NaN < -Inf < ... < -0 < +0 < ... < +Inf < +NaN, NaNs by payload.
+ * The sort is a top-down stable merge sort driven by that comparison.
+ * type: 1 = i32, 2 = f32, 4 = i64, 5 = f64 (keys given as raw bits). */
+static int typed_less(uint64_t a, uint64_t b, int type) {
+    int width = (type == 1 || type == 2) ? 32 : 64;
+    uint64_t sign = (uint64_t)1 << (width - 1);
+    uint64_t mag = sign - 1;
+    int sa = (a & sign) != 0, sb = (b & sign) != 0;
+    if (type == 1 || type == 4) {
+        if (sa != sb) return sa; /* the negative one is smaller */
+        return (a & (sign | mag)) < (b & (sign | mag)); /* same sign: two's complement order is bit order */
+    }
+    if (sa != sb) return sa;
+    if (sa) return (a & mag) > (b & mag);
+    return (a & mag) < (b & mag);
+}
+
+static void typed_merge_sort(uint64_t* k, uint32_t* v, size_t n, uint64_t* tk, uint32_t* tv, int type) {
+    if (n < 2) return;
+    size_t h = n / 2;
+    typed_merge_sort(k, v, h, tk, tv, type);
+    typed_merge_sort(k + h, v ? v + h : NULL, n - h, tk, tv, type);
+    size_t i = 0, j = h, o = 0;
+    while (i < h || j < n) {
+        /* take from the right only when strictly smaller: equal keys keep input order */
+        int right = j < n && (i >= h || typed_less(k[j], k[i], type));
+        size_t s = right ? j++ : i++;
+        tk[o] = k[s];
+        if (v) tv[o] = v[s];
+        ++o;
+    }
+    memcpy(k, tk, n * sizeof(uint64_t));
+    if (v) memcpy(v, tv, n * sizeof(uint32_t));
+}
+
+int oracle_sort_typed(void* keys, int type, uint32_t* vals, size_t n) {
+    if (type != 1 && type != 2 && type != 4 && type != 5) return -1;
+    int w32 = type == 1 || type == 2;
+    uint64_t* k = (uint64_t*)malloc((n ? n : 1) * sizeof(uint64_t));
+    uint64_t* tk = (uint64_t*)malloc((n ? n : 1) * sizeof(uint64_t));
+    uint32_t* tv = vals ? (uint32_t*)malloc((n ? n : 1) * sizeof(uint32_t)) : NULL;
+    if (!k || !tk || (vals && !tv)) {
+        free(k);
+        free(tk);
+        free(tv);
+        return -2;
+    }
+    for (size_t i = 0; i < n; ++i) k[i] = w32 ? (uint64_t)((uint32_t*)keys)[i] : ((uint64_t*)keys)[i];
+    typed_merge_sort(k, vals, n, tk, tv, type);
+    for (size_t i = 0; i < n; ++i) {
+        if (w32) ((uint32_t*)keys)[i] = (uint32_t)k[i];
+        else ((uint64_t*)keys)[i] = k[i];
+    }
+    free(k);
+    free(tk);
+    free(tv);
+    return 0;
+}
