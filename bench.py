@@ -25,7 +25,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-MODELS = {0: "piecewise-linear CDF", 1: "1-32-1 MLP CDF"}
+MODELS = {0: "piecewise-linear CDF", 1: "1-32-1 MLP CDF", 2: "regular sampling, no trained model"}
 METRIC = "Gkeys/s (u32 n=2^28) & % HBM roofline; learned/batched vs plain LSD, bit-exact"
 UNIT = "Gkeys/s"
 N = 1 << 28
@@ -587,8 +587,8 @@ def main():
                     help="uniform: the benchmark; learned / segmented: secondary comparisons with plain LSD; "
                          "small: the 65,536-key case and the block networks on 1,024 keys")
     ap.add_argument("--nbuckets", type=int, default=0, help="learned: bucket count (0: the library's choice)")
-    ap.add_argument("--model", type=int, default=0, choices=[0, 1],
-                    help="learned: 0 = piecewise-linear CDF, 1 = the 1-32-1 MLP CDF")
+    ap.add_argument("--model", type=int, default=0, choices=[0, 1, 2],
+                    help="learned: 0 = piecewise-linear CDF, 1 = the 1-32-1 MLP CDF, 2 = regular sampling (untrained)")
     ap.add_argument("--dist", default="lognormal", choices=["zipf", "lognormal", "gmm", "range48"],
                     help="learned: key distribution; learned64: range48 for keys on [0, 2^48)")
     args = ap.parse_args()

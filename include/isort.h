@@ -76,8 +76,11 @@ ISORT_API const char* isort_status_string(isort_status s);
  * counts between processors), and ranks and scatters the keys (and payloads)
  * chunk by chunk (one read, one write). Digits wider than the chunked round's
  * tables take single-pass rounds (all rounds' counts from one read, tile
- * offsets by a bounded decoupled look-back). radix_bits above 12 returns
- * ISORT_ERR_UNSUPPORTED.
+ * offsets by a bounded decoupled look-back). A round of radix 2^13..2^16 (the
+ * paper's r = 2^16 among them) runs as two stable passes over the low and
+ * high halves of its digit (16 = 8 + 8, 13 = 7 + 6), which together are that
+ * round's stable count-sort: a single 2^16-way pass would need 2^16 counters
+ * per chunk, more than an SM's shared memory.
  * In place: on ISORT_OK keys (and vals) hold the sorted result.
  * ------------------------------------------------------------------------- */
 ISORT_API isort_status isort_radix(uint32_t* keys, uint32_t* vals, size_t n, int key_bits, int radix_bits, void* stream);
@@ -91,6 +94,22 @@ ISORT_API isort_status isort_radix_copy(const uint32_t* keys_in, const uint32_t*
                               uint32_t* vals_out, size_t n, int key_bits, int radix_bits, void* stream);
 ISORT_API isort_status isort_radix_copy_u64(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
                                   uint32_t* vals_out, size_t n, int key_bits, int radix_bits, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Typed keys. The paper sorts unsigned integers; signed integers and IEEE 754
+ * floats are sorted by the same rounds through an order-preserving map of
+ * their bits, applied in place before the rounds and undone after them:
+ * signed: flip the sign bit; float: flip every bit of a key whose sign bit is
+ * set, else only the sign bit. Orders: integers by value; floats by IEEE 754
+ * totalOrder (-NaN < -Inf < ... < -0 < +0 < ... < +Inf < +NaN; NaNs by their
+ * payload bits). Stable: equal keys (same bits) keep their input order.
+ * key_type: ISORT_KEY_U32, _I32, _F32 (4-byte keys), _U64, _I64, _F64
+ * (8-byte keys); keys and vals (optional u32 payload) are DEVICE memory,
+ * sorted in place over the full key width; radix_bits 1..16.
+ * ------------------------------------------------------------------------- */
+enum { ISORT_KEY_U32 = 0, ISORT_KEY_I32 = 1, ISORT_KEY_F32 = 2, ISORT_KEY_U64 = 3, ISORT_KEY_I64 = 4, ISORT_KEY_F64 = 5 };
+ISORT_API isort_status isort_radix_typed(void* keys, int key_type, uint32_t* vals, size_t n, int radix_bits,
+                                         void* stream);
 
 /* ---------------------------------------------------------------------------
  * The two primitives of a count-sort round (Section 3, "Serial radix-r"), for
@@ -180,7 +199,11 @@ ISORT_API isort_status isort_segmented(uint32_t* keys, uint32_t* vals, const uin
  * doubled up to 32768 while n / nbuckets > 16,384; for u64 keys > 8,192);
  * model 0 = the piecewise-linear CDF of step 2; model 1 = a 1-32-1 monotone
  * MLP CDF instead (see isort_mlp_train), trained on every 16th point of the
- * sorted sample and tabulated as the 257 knots (X_k, Y_k) steps 3-4 read.
+ * sorted sample and tabulated as the 257 knots (X_k, Y_k) steps 3-4 read;
+ * model 2 = no training (the method without a learned model): the table of
+ * step 2's start, knots at the sample's quantiles j/256 with values j/256,
+ * i.e. regular sampling (Section 2) with 255 evenly spaced sample keys as
+ * splitters, each interval split evenly in key space when nbuckets > 256.
  * n < 2^18 sorts with the plain rounds. If more than half of the keys fall in
  * buckets beyond the on-chip capacity (65,536 keys) the call sorts with the
  * plain rounds instead (stats->fell_back_to_lsd = 1); fewer such buckets are

@@ -73,6 +73,7 @@ SIGNATURES = [
     ("isort_learned_u64", _i32, [_vp, _vp, _sz, _i32, _i32, _i32, _vp, _vp]),
     ("isort_cdf_train", _i32, [_vp, ctypes.c_uint32, _i32, _vp, _vp, _vp, _vp, _vp]),
     ("isort_cdf_loss_grad", _i32, [_vp, ctypes.c_uint32, _vp, _vp, _vp, _vp]),
+    ("isort_radix_typed", _i32, [_vp, _i32, _vp, ctypes.c_size_t, _i32, _vp]),
     ("isort_mlp_train", _i32, [_vp, ctypes.c_uint32, _i32, _vp, _vp, _vp, _vp, _vp]),
     ("isort_mlp_loss_grad", _i32, [_vp, ctypes.c_uint32, _vp, _vp, _vp, _vp]),
     ("isort_cdf_splitters", _i32, [_vp, _vp, _i32, _i32, _i32, _vp, _vp]),
@@ -282,6 +283,23 @@ def cdf_loss_grad(u, theta, stream=None):
     _check(load().isort_cdf_loss_grad(_ptr(u), u.numel(), _ptr(theta), _ptr(grad), _ptr(loss), _stream(stream)),
            "isort_cdf_loss_grad")
     return loss, grad
+
+
+KEY_TYPES = {"u32": 0, "i32": 1, "f32": 2, "u64": 3, "i64": 4, "f64": 5}
+
+
+def radix_typed(keys, key_type: str, vals=None, radix_bits: int = 8, stream=None):
+    """Stable in-place sort of typed keys (a 4- or 8-byte device tensor whose
+    bits are key_type: u32, i32, f32, u64, i64 or f64); floats by IEEE 754
+    totalOrder. Returns (keys, vals)."""
+    if key_type not in KEY_TYPES:
+        raise ValueError(f"key_type must be one of {sorted(KEY_TYPES)}")
+    want = 4 if key_type.endswith("32") else 8
+    if keys.element_size() != want:
+        raise TypeError(f"{key_type} keys need {want}-byte elements, got {keys.element_size()}")
+    _check(load().isort_radix_typed(_ptr(keys), KEY_TYPES[key_type], _ptr(vals), keys.numel(), radix_bits,
+                                    _stream(stream)), "isort_radix_typed")
+    return keys, vals
 
 
 def mlp_train(sorted_sample, key_bits: int = 32, stream=None):

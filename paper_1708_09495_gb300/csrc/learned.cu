@@ -693,7 +693,7 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
     if (st != ISORT_OK) return fail(st);
 
     // 2. train the model (both leave their CDF as the table X, Y)
-    if (model == 0) {
+    if (model == 0 || model == 2) {
         {
             LaunchScope ls("cdf_init", s);
             k_normalise<K><<<(m / kFitStride + 255) / 256, 256, 0, s>>>(sample, m / kFitStride, kFitStride, scale, u);
@@ -701,7 +701,10 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
             ce = cudaGetLastError();
             if (ce != cudaSuccess) return fail(from_cuda(ce));
         }
-        st = launch_fit(u, m / kFitStride, theta, X, Y, losses, nullptr, nullptr, kTrainSteps, s);
+        // model 2 (regular sampling): no steps, the table of the start; its
+        // loss lands where the record of a trained model keeps it
+        st = model == 0 ? launch_fit(u, m / kFitStride, theta, X, Y, losses, nullptr, nullptr, kTrainSteps, s)
+                        : launch_fit(u, m / kFitStride, theta, X, Y, losses + kTrainSteps, nullptr, nullptr, 0, s);
     } else {
         st = mlp_model<K>(sample, m, scale, u, theta, X, Y, losses, s);
     }
@@ -760,7 +763,7 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
     stats->fixups = 0;  // the bucket function is monotone: nothing to correct
     stats->train_loss = h_loss[kTrainSteps];
     stats->train_loss_initial = h_loss[kTrainSteps + 1];
-    stats->train_steps = kTrainSteps;
+    stats->train_steps = model == 2 ? 0 : kTrainSteps;
     stats->nbuckets = B;
     if (stats->overflow_fraction > 0.5) {
         stats->fell_back_to_lsd = 1;
@@ -884,7 +887,7 @@ isort_status learned_entry(K* keys, uint32_t* vals, size_t n, int key_bits, int 
         while (nbuckets < kMaxBuckets && (uint64_t)nbuckets * mean_max < n) nbuckets <<= 1;
     }
     if (nbuckets < 2 || nbuckets > kMaxBuckets) return ISORT_ERR_INVALID_ARG;
-    if (model != 0 && model != 1) return ISORT_ERR_INVALID_ARG;
+    if (model < 0 || model > 2) return ISORT_ERR_INVALID_ARG;
     if (n >= (size_t(1) << 30)) return ISORT_ERR_UNSUPPORTED;
     if (n > 1 && !keys) return ISORT_ERR_INVALID_ARG;
     if (n <= 1) return ISORT_OK;

@@ -922,12 +922,12 @@ isort_status radix_device(const K* kin, const uint32_t* vin, K* kout, uint32_t* 
     const int key_width = (int)sizeof(K) * 8;
     const int rounds = (key_bits + rb - 1) / rb;
     const int bins = 1 << rb;
-    if (rb > 12) return ISORT_ERR_UNSUPPORTED;
-    if (tune().algo == 1 && peek_stall_tile() < 0) {
-        // chunked rounds; wide digits whose tables do not fit on chip take
-        // the single-pass rounds below (refused before any work is enqueued)
+    if (rb > 12 || (tune().algo == 1 && peek_stall_tile() < 0)) {
+        // chunked rounds (which also take radix 2^13..2^16, as two passes per
+        // round); wide digits whose tables do not fit on chip take the
+        // single-pass rounds below (refused before any work is enqueued)
         const isort_status st = radix_device_rts<K>(kin, vin, kout, vout, n, key_bits, rb, s);
-        if (st != ISORT_ERR_UNSUPPORTED) return st;
+        if (st != ISORT_ERR_UNSUPPORTED || rb > 12) return st;
     }
     const bool vals = vin != nullptr;
     const bool inplace = (const void*)kin == (const void*)kout;

@@ -231,11 +231,29 @@ template <typename K>
 isort_status radix_device_rts(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n, int key_bits,
                               int rb, cudaStream_t s, int shape) {
     const int key_width = (int)sizeof(K) * 8;
-    const int rounds = (key_bits + rb - 1) / rb;
-    const int bins = 1 << rb;
+    // The passes: one per round of ceil(key_bits / rb); a round whose digit is
+    // wider than 12 bits (radix 2^13..2^16) runs as two stable passes over
+    // its low and high halves (16 = 8 + 8, 13 = 7 + 6): together they are the
+    // round's stable count-sort on the whole digit. A one-pass 2^16-way round
+    // would need 2^16 counters per chunk (256 KB, above the shared memory of
+    // an SM) and 2^16 x chunks partly written output runs.
+    int pass_shift[64], pass_width[64];
+    int rounds = 0, max_width = 0;
+    for (int shift = 0; shift < key_bits; shift += rb) {
+        const int w = std::min(rb, key_bits - shift);
+        const int lo = w > 12 ? (w + 1) / 2 : w;
+        pass_shift[rounds] = shift;
+        pass_width[rounds++] = lo;
+        if (w > lo) {
+            pass_shift[rounds] = shift + lo;
+            pass_width[rounds++] = w - lo;
+        }
+        max_width = std::max(max_width, lo);
+    }
+    const int bins = 1 << max_width;
     const bool vals = vin != nullptr;
     const bool inplace = (const void*)kin == (const void*)kout;
-    const int sh = shape >= 0 ? shape : autotuned_shape<K>(kin, vals, n, key_bits, rb, s);
+    const int sh = shape >= 0 ? shape : autotuned_shape<K>(kin, vals, n, key_bits, max_width, s);
     int per_sm = 0;
     isort_status st = vals ? sweep_dispatch<K, true>(sh, true, bins, &per_sm, nullptr, 0, s)
                            : sweep_dispatch<K, false>(sh, true, bins, &per_sm, nullptr, 0, s);
@@ -298,8 +316,8 @@ isort_status radix_device_rts(const K* kin, const uint32_t* vin, K* kout, uint32
             dk = wk[d % 2];
             dv = wv[d % 2];
         }
-        const int shift = d * rb;
-        const int width = std::min(rb, key_bits - shift);
+        const int shift = pass_shift[d];
+        const int width = pass_width[d];
         {
             LaunchScope ls("chunk_hist", s);
             k_chunk_hist<K><<<chunks, kChunkHistThreads, hist_smem, s>>>(src_k, (uint32_t)n, shift, width,

@@ -158,7 +158,7 @@ def test_learned_rejects(cuda_lib):
 
     k = torch.zeros(1 << 19, dtype=torch.int32, device="cuda")
     with pytest.raises(cuda_lib.IsortError, match="INVALID|invalid"):
-        cuda_lib.learned(k, model=2)
+        cuda_lib.learned(k, model=3)
     with pytest.raises(cuda_lib.IsortError):
         cuda_lib.learned(k, nbuckets=65536)
     big = torch.full((1 << 19,), 1 << 21, dtype=torch.int32, device="cuda")
@@ -267,3 +267,33 @@ def test_model_beats_equal_width_buckets(cuda_lib, kind):
     plain = counts.max() / (keys.size / 4096)
     st = cuda_lib.learned(to_dev(keys), None)
     assert st["imbalance_max_over_mean"] * 4 < plain, (st["imbalance_max_over_mean"], plain)
+
+
+# ------------------------------------------------------------------ without the model
+
+@pytest.mark.parametrize("kind", ["lognormal", "gmm"])
+def test_regular_sampling_matches_oracle(cuda_lib, kind):
+    """model 2: the untrained quantile table (regular sampling)."""
+    keys = _keys(kind, (1 << 21) + 5)
+    v = gen.iota_u32(keys.size)
+    dk, dv = to_dev(keys), to_dev(v)
+    st = cuda_lib.learned(dk, dv, model=2)
+    ek, ev = oracle.lsd(keys, v, 0, 8)
+    assert np.array_equal(to_np(dk, np.uint32), ek) and np.array_equal(to_np(dv, np.uint32), ev)
+    assert st["train_steps"] == 0 and st["train_loss"] == st["train_loss_initial"]
+
+
+@pytest.mark.parametrize("kind", ["zipf", "lognormal", "gmm"])
+def test_trained_model_vs_regular_sampling(cuda_lib, kind):
+    """What training adds to the method without it: the trained piecewise-
+    linear model starts from the regular-sampling table and keeps the best
+    parameters, so its sample loss is never higher; both sorts are exact."""
+    keys = _keys(kind)
+    ek, _ = oracle.lsd(keys, None, 0, 8)
+    res = {}
+    for model in (2, 0, 1):
+        dk = to_dev(keys)
+        res[model] = cuda_lib.learned(dk, None, model=model)
+        assert np.array_equal(to_np(dk, np.uint32), ek)
+    print(kind, {m: (r["train_loss"], r["imbalance_max_over_mean"]) for m, r in res.items()})
+    assert res[0]["train_loss"] <= res[2]["train_loss"] * (1 + 1e-5)

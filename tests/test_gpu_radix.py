@@ -57,7 +57,7 @@ def test_sizes_pairs(cuda_lib, n, rb):
     check(cuda_lib, keys, vals, 32, rb)
 
 
-@pytest.mark.parametrize("rb", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12])
+@pytest.mark.parametrize("rb", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16])
 @pytest.mark.parametrize("key_bits", [32, 20, 13, 1])
 def test_all_digit_widths(cuda_lib, rb, key_bits):
     n = 3 * TILE + 123
@@ -67,7 +67,7 @@ def test_all_digit_widths(cuda_lib, rb, key_bits):
     check(cuda_lib, keys, None, key_bits, rb)
 
 
-@pytest.mark.parametrize("key_bits,rb", [(64, 8), (48, 8), (64, 11), (40, 12), (33, 5)])
+@pytest.mark.parametrize("key_bits,rb", [(64, 8), (48, 8), (64, 11), (40, 12), (33, 5), (64, 16), (48, 13)])
 @pytest.mark.parametrize("n", [5000, 100_003])
 def test_u64(cuda_lib, key_bits, rb, n):
     keys = gen.uniform_u64(n, key_bits, 5 + n, 0)
@@ -357,3 +357,15 @@ def test_autotune_picks_a_shape_and_caches_it(cuda_lib, tmp_path):
         assert len([ln for ln in open(path).read().split("\n") if ln.strip()]) == len(rows)
     finally:
         cuda_lib.autotune(False)
+
+
+@pytest.mark.parametrize("rb", [16, 13])
+def test_wide_radix_against_the_paper_radix_rounds(cuda_lib, rb):
+    """Radix 2^16 (and 2^13): the GPU runs each round as two stable passes
+    over the halves of the digit; the oracle runs the paper's 2^16-way (2^13)
+    count-sort rounds directly. Several chunks and a ragged tail."""
+    n = (1 << 22) + 4097
+    keys = gen.uniform_u32(n, 32, 1600 + rb, 0)
+    keys[::5] = keys[11]
+    vals = np.arange(n, dtype=np.uint32)
+    check(cuda_lib, keys, vals, 32, rb)
