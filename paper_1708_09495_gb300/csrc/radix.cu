@@ -55,11 +55,13 @@ static Tune load_tune() {
         else if (!strcmp(key, "algo")) t.algo = val;
         else if (!strcmp(key, "sweep8")) t.sweep_small = val;
         else if (!strcmp(key, "sweep11")) t.sweep_large = val;
+        else if (!strcmp(key, "split")) t.split = val;
         p += used;
         if (*p == ',') ++p;
     }
     if (t.sweep_small < 0 || t.sweep_small >= 5) t.sweep_small = 4;
     if (t.sweep_large < 0 || t.sweep_large >= 4) t.sweep_large = 2;
+    if (t.split < 8 || t.split > 16) t.split = 8;
     auto built = [](int sh) { return sh == 0 || sh == 1 || sh == 4 || sh == 9 || sh == 10; };
     if (!built(t.shape_small)) t.shape_small = 4;
     if (!built(t.shape_large)) t.shape_large = 1;

@@ -84,8 +84,11 @@ template <typename K, bool VALS, int THREADS, int ITEMS>
 isort_status sweep_hw_or_generic(bool occupancy_only, int bins, int* per_sm, const SweepArgs* a, uint32_t chunks,
                                  cudaStream_t s) {
     if constexpr (sizeof(K) == 4) {  // with u64 keys the padded buffers leave one CTA per SM
-        if (bins == kHwBins) {
+        if (bins <= kHwBins) {
             if (occupancy_only) return sweep_occupancy_hw<K, VALS, THREADS, ITEMS>(per_sm);
+            int tmp = 0;  // sets the kernel's shared-memory attribute (the sizing may have been for a wider pass)
+            const isort_status so = sweep_occupancy_hw<K, VALS, THREADS, ITEMS>(&tmp);
+            if (so != ISORT_OK) return so;
             return launch_sweep_hw<K, VALS, THREADS, ITEMS>(*a, chunks, s);
         }
     }
@@ -232,16 +235,18 @@ isort_status radix_device_rts(const K* kin, const uint32_t* vin, K* kout, uint32
                               int rb, cudaStream_t s, int shape) {
     const int key_width = (int)sizeof(K) * 8;
     // The passes: one per round of ceil(key_bits / rb); a round whose digit is
-    // wider than 12 bits (radix 2^13..2^16) runs as two stable passes over
-    // its low and high halves (16 = 8 + 8, 13 = 7 + 6): together they are the
-    // round's stable count-sort on the whole digit. A one-pass 2^16-way round
-    // would need 2^16 counters per chunk (256 KB, above the shared memory of
-    // an SM) and 2^16 x chunks partly written output runs.
+    // wider than 8 bits runs as two stable passes over its low and high
+    // halves (11 = 6 + 5, 16 = 8 + 8): together they are the round's stable
+    // count-sort on the whole digit. A one-pass round of 9..12 bits scans
+    // 2^w counters per warp on every tile and keeps one CTA per SM (measured
+    // slower than its two passes); a one-pass 2^16-way round would need 2^16
+    // counters per chunk (256 KB, above the shared memory of an SM).
+    const int split = std::min(tune().split, 12);
     int pass_shift[64], pass_width[64];
     int rounds = 0, max_width = 0;
     for (int shift = 0; shift < key_bits; shift += rb) {
         const int w = std::min(rb, key_bits - shift);
-        const int lo = w > 12 ? (w + 1) / 2 : w;
+        const int lo = w > split ? (w + 1) / 2 : w;
         pass_shift[rounds] = shift;
         pass_width[rounds++] = lo;
         if (w > lo) {

@@ -466,6 +466,7 @@ __device__ __forceinline__ void hw_tile(const SweepArgs& a, K* s_keys, uint32_t*
     constexpr int kPerHalf = kGroups / Cfg::kHalves;
     const int tid = threadIdx.x, lane = tid & 31, hw = tid >> 4, l16 = lane & 15;
     const int shift = a.shift;
+    const uint32_t dmask = (uint32_t)a.bins - 1u;  // digits of up to 8 bits
     uint32_t* my_w = s_word + hw * kHwBins;
     const uint32_t bit = 1u << l16, lt16 = bit - 1u;
     K kreg[ITEMS];
@@ -480,7 +481,7 @@ __device__ __forceinline__ void hw_tile(const SweepArgs& a, K* s_keys, uint32_t*
         const K k = valid ? s_keys[p] : (K)0;
         kreg[i] = k;
         if constexpr (VALS) vreg[i] = valid ? s_vals[p] : 0u;
-        const uint32_t d = valid ? (uint32_t)(k >> shift) & (kHwBins - 1) : 0u;
+        const uint32_t d = valid ? (uint32_t)(k >> shift) & dmask : 0u;
         if (valid) atomicAdd(&my_w[d], 0x10000u | bit);
         __syncwarp();
         const uint32_t x = valid ? my_w[d] : 0u;
@@ -538,7 +539,7 @@ __device__ __forceinline__ void hw_tile(const SweepArgs& a, K* s_keys, uint32_t*
         const uint32_t j = (uint32_t)(tid + i * THREADS);
         if (FULL || j < tile_n) {
             const K k = s_keys[j];
-            const uint32_t d = (uint32_t)(k >> shift) & (kHwBins - 1);
+            const uint32_t d = (uint32_t)(k >> shift) & dmask;
             const uint32_t dst = s_delta[d] + j;
             if (dst < a.n) {
                 keys_out[dst] = k;
@@ -583,7 +584,8 @@ __global__ void __launch_bounds__(THREADS, (THREADS == 512 && ITEMS <= 8) || THR
     const K* keys_in = static_cast<const K*>(a.keys_in);
 
     for (int i = tid; i < kGroups * kHwBins; i += THREADS) s_word[i] = 0u;
-    for (int d = tid; d < kHwBins; d += THREADS) s_run[d] = a.chunk_off[(size_t)blockIdx.x * kHwBins + d];
+    for (int d = tid; d < kHwBins; d += THREADS)
+        s_run[d] = d < a.bins ? a.chunk_off[(size_t)blockIdx.x * a.bins + d] : 0u;  // [chunks][bins]
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
