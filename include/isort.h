@@ -13,8 +13,12 @@
  *   - keys / vals are caller-owned buffers of n elements. They may live in
  *     device memory (cudaMalloc, torch tensors, managed memory) or in host
  *     memory (pinned or pageable): host buffers are staged through device
- *     memory inside the call and the call then returns only after the result
- *     is back in the host buffers. vals == NULL means "keys only"; otherwise
+ *     memory inside the call. In the synchronous mode the call returns after
+ *     the result is back in the host buffers; with isort_set_sync(0) it
+ *     returns once the copies and the sort are enqueued, and the host buffers
+ *     stay in use until `stream` reaches the end of that work (with pinned
+ *     buffers, calls on different streams then overlap their copies in, sorts
+ *     and copies out). vals == NULL means "keys only"; otherwise
  *     vals is a uint32 payload that moves with its key.
  *   - stream is a cudaStream_t (NULL = the legacy default stream). Work is
  *     enqueued on it. In the default synchronous-status mode (see

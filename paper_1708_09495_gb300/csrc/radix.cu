@@ -1028,34 +1028,38 @@ isort_status radix_device(const K* kin, const uint32_t* vin, K* kout, uint32_t* 
 
 // Entry: validates, stages host buffers through device memory if needed.
 // A copy ordered on `s`, cut into up to kCopyStreams pieces of at least 64 MiB
-// that run on the calling thread's auxiliary streams for this device.
+// that run on auxiliary streams kept per (thread, device, calling stream), so
+// that the copies of calls made on different streams can overlap.
 constexpr int kCopyStreams = 4;
+constexpr size_t kMaxCopySets = 16;  // calling streams with their own auxiliary streams, per thread
 
 struct CopyStreams {
-    int device = -1;
     cudaStream_t st[kCopyStreams] = {};
     cudaEvent_t ev[kCopyStreams + 1] = {};
 };
 
-thread_local CopyStreams t_copy;
+thread_local std::map<std::pair<int, cudaStream_t>, CopyStreams> t_copy;
 
 cudaError_t copy_split(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    const size_t piece_min = size_t(64) << 20;
+    const int pieces = (int)std::min<size_t>(kCopyStreams, std::max<size_t>(1, bytes / piece_min));
+    if (pieces <= 1) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s);
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce != cudaSuccess) return ce;
-    CopyStreams& cs = t_copy;
-    if (cs.device != dev) {  // created once per thread and device, kept for the process
+    auto it = t_copy.find({dev, s});
+    if (it == t_copy.end()) {
+        if (t_copy.size() >= kMaxCopySets) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s);
+        CopyStreams cs;  // created once per (thread, device, stream), kept for the process
         for (int i = 0; i < kCopyStreams; ++i) {
             if (cudaStreamCreateWithFlags(&cs.st[i], cudaStreamNonBlocking) != cudaSuccess) return cudaGetLastError();
         }
         for (int i = 0; i <= kCopyStreams; ++i) {
             if (cudaEventCreateWithFlags(&cs.ev[i], cudaEventDisableTiming) != cudaSuccess) return cudaGetLastError();
         }
-        cs.device = dev;
+        it = t_copy.emplace(std::make_pair(dev, s), cs).first;
     }
-    const size_t piece_min = size_t(64) << 20;
-    const int pieces = (int)std::min<size_t>(kCopyStreams, std::max<size_t>(1, bytes / piece_min));
-    if (pieces <= 1) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s);
+    CopyStreams& cs = it->second;
     ce = cudaEventRecord(cs.ev[kCopyStreams], s);  // the copies start after the work before them
     const size_t step = align_up((bytes + pieces - 1) / pieces, 4096);
     for (int i = 0; i < pieces && ce == cudaSuccess; ++i) {
@@ -1120,8 +1124,10 @@ isort_status radix_entry(const K* kin, const uint32_t* vin, K* kout, uint32_t* v
         }
     }
     scratch_free(st_buf, s);
+    // asynchronous status mode: the call returns once everything is enqueued;
+    // the host buffers are in use until `s` reaches this point
+    if (!was_sync) return st;
     cudaError_t se = cudaStreamSynchronize(s);
-    (void)was_sync;
     if (st == ISORT_OK && se != cudaSuccess) st = from_cuda(se);
     return st;
 }

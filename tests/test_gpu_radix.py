@@ -173,6 +173,41 @@ def test_host_buffers_large_split_copies(cuda_lib):
     assert np.array_equal(ko, rk) and np.array_equal(vo, rv)
 
 
+def test_host_buffers_asynchronous_calls_on_several_streams(cuda_lib):
+    """Asynchronous status mode: host-to-host calls return after enqueueing,
+    several are in flight on different streams (their copies and sorts
+    overlap), each writes its own pinned output; all results are exact once
+    the streams are done, and the device status stays clear."""
+    import torch
+
+    lib = cuda_lib.load()
+    n = (1 << 24) + 3
+    inputs = [gen.uniform_u32(n, 32, 40 + i, 0) for i in range(3)]
+    vals = np.arange(n, dtype=np.uint32)
+    hk = [torch.from_numpy(k.view(np.int32).copy()).pin_memory() for k in inputs]
+    hv = torch.from_numpy(vals.view(np.int32).copy()).pin_memory()
+    ko = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in range(6)]
+    vo = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in range(6)]
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    lib.isort_set_sync(0)
+    try:
+        for i in range(6):
+            j = i % 3
+            rc = lib.isort_radix_copy(ctypes.c_void_p(hk[j].data_ptr()), ctypes.c_void_p(hv.data_ptr()),
+                                      ctypes.c_void_p(ko[i].data_ptr()), ctypes.c_void_p(vo[i].data_ptr()), n, 32, 8,
+                                      ctypes.c_void_p(streams[j].cuda_stream))
+            assert rc == 0
+        torch.cuda.synchronize()
+    finally:
+        lib.isort_set_sync(1)
+    assert lib.isort_device_status(1, None) == 0
+    for j in range(3):
+        rk, rv = oracle.lsd(inputs[j], vals, 32, 8)
+        for i in (j, j + 3):
+            assert np.array_equal(ko[i].numpy().view(np.uint32), rk)
+            assert np.array_equal(vo[i].numpy().view(np.uint32), rv)
+
+
 def test_key_range_violation_leaves_buffers(cuda_lib):
     import torch
 
