@@ -56,6 +56,7 @@ static Tune load_tune() {
         else if (!strcmp(key, "sweep8")) t.sweep_small = val;
         else if (!strcmp(key, "sweep11")) t.sweep_large = val;
         else if (!strcmp(key, "split")) t.split = val;
+        else if (!strcmp(key, "small")) t.small = val;
         p += used;
         if (*p == ',') ++p;
     }
@@ -907,6 +908,11 @@ bool valid_widths(int key_width, int& key_bits, int rb) {
 
 }  // namespace
 
+// The whole sort of up to 8 x 8192 u32 keys on one cluster (seg.cu).
+constexpr size_t kSmallSortMax = 8 * 8192;
+isort_status radix_small_u32(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout, uint32_t n,
+                             int key_bits, cudaStream_t s);
+
 // The chunked reduce-then-scan rounds (rts.cu).
 template <typename K>
 isort_status radix_device_rts(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n, int key_bits,
@@ -924,6 +930,11 @@ isort_status radix_device(const K* kin, const uint32_t* vin, K* kout, uint32_t* 
     const int key_width = (int)sizeof(K) * 8;
     const int rounds = (key_bits + rb - 1) / rb;
     const int bins = 1 << rb;
+    if constexpr (sizeof(K) == 4) {
+        // up to 65,536 keys: all rounds on chip in one launch
+        if (n <= kSmallSortMax && rb == 8 && tune().small && peek_stall_tile() < 0)
+            return radix_small_u32(kin, vin, kout, vout, (uint32_t)n, key_bits, s);
+    }
     if (rb > 12 || (tune().algo == 1 && peek_stall_tile() < 0)) {
         // chunked rounds (which also take radix 2^13..2^16, as two passes per
         // round); wide digits whose tables do not fit on chip take the

@@ -153,6 +153,9 @@ struct SegArgsT {
     int key_bits;
     const K* seg_lo;          // optional: segment s's keys lie in [seg_lo[s], seg_lo[s] + 2^seg_bits[s])
     const uint8_t* seg_bits;  //   and are sorted on key - seg_lo[s] over seg_bits[s] bits
+    uint32_t single_n = 0;    // > 0: one segment [0, single_n) (off, list and counts unused)
+    K* keys_out = nullptr;    // single segment: the result goes here (keys / vals only read)
+    uint32_t* vals_out = nullptr;
 };
 using ClusterArgs = SegArgsT<uint32_t>;
 
@@ -183,7 +186,7 @@ __global__ void __launch_bounds__(kSegThreads, 2) k_seg_cluster(ClusterArgs a) {
     cg::cluster_group cluster = cg::this_cluster();
     const uint32_t r = C == 1 ? 0u : cluster.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t cnt = a.ctl->counts[a.cls];
+    const uint32_t cnt = a.single_n ? 1u : a.ctl->counts[a.cls];
 
     for (int i = tid; i < kSegWarps * kSegBins; i += kSegThreads) {
         s_cnt[i] = 0;
@@ -195,9 +198,9 @@ __global__ void __launch_bounds__(kSegThreads, 2) k_seg_cluster(ClusterArgs a) {
     // (every CTA of a cluster walks the same entries)
     const uint32_t nclusters = gridDim.x / C;
     for (uint32_t q = blockIdx.x / C; q < cnt; q += nclusters) {
-        const uint32_t s = a.list[q];
-        const uint64_t lo = a.off[s];
-        const uint32_t L = (uint32_t)(a.off[s + 1] - lo);
+        const uint32_t s = a.single_n ? 0u : a.list[q];
+        const uint64_t lo = a.single_n ? 0ull : a.off[s];
+        const uint32_t L = a.single_n ? a.single_n : (uint32_t)(a.off[s + 1] - lo);
         const uint32_t kbase = a.seg_lo ? a.seg_lo[s] : 0u;
         const int sbits = a.seg_bits ? (int)a.seg_bits[s] : a.key_bits;
         const int rounds = (sbits + 7) / 8;
@@ -337,12 +340,14 @@ __global__ void __launch_bounds__(kSegThreads, 2) k_seg_cluster(ClusterArgs a) {
             __syncthreads();
             continue;
         }
+        uint32_t* ok = a.keys_out ? a.keys_out + lo + my_lo : gk;
+        uint32_t* ov = VALS ? (a.vals_out ? a.vals_out + lo + my_lo : gv) : nullptr;
 #pragma unroll
         for (int i = 0; i < kSegItems; ++i) {
             const uint32_t j = (uint32_t)(warp * kSegItems * 32 + i * 32 + lane);
             if (j < my_n) {
-                gk[j] = k[i];
-                if constexpr (VALS) gv[j] = v[i];
+                ok[j] = k[i];
+                if constexpr (VALS) ov[j] = v[i];
             }
         }
     }
@@ -733,6 +738,29 @@ isort_status launch_cluster(bool vals, const ClusterArgs& a, cudaStream_t s) {
     return ISORT_OK;
 }
 
+// One cluster of C CTAs sorting the single segment a.single_n keys long.
+template <int C>
+isort_status launch_cluster_single(bool vals, const ClusterArgs& a, cudaStream_t s) {
+    const size_t smem = cluster_smem_bytes(vals);
+    auto kern = vals ? k_seg_cluster<C, true> : k_seg_cluster<C, false>;
+    ISORT_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.blockDim = dim3(kSegThreads);
+    cfg.gridDim = dim3(C);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    LaunchScope ls(C == 1 ? "small_sort1" : C == 2 ? "small_sort2" : C == 4 ? "small_sort4" : "small_sort8", s);
+    ISORT_TRY_CUDA(cudaLaunchKernelEx(&cfg, kern, a));
+    return ISORT_OK;
+}
+
 template <int P>
 isort_status launch_btn_cta(uint32_t* keys, uint32_t* vals, const uint64_t* off, uint32_t* lists, uint32_t nseg,
                             SegCtl* ctl, int cls, uint32_t range_mask, cudaStream_t s) {
@@ -960,6 +988,37 @@ isort_status segmented_entry(uint32_t* keys, uint32_t* vals, const uint64_t* off
 
 // The finishing step of the learned-bucket sort: every bucket is a segment
 // whose keys lie in [seg_lo[s], seg_lo[s] + 2^seg_bits[s]).
+// The whole radix-2^8 sort of n <= 8 * 8192 u32 keys (+ payload) in one
+// launch, from kin/vin to kout/vout (the same buffers: in place): the
+// count-sort rounds run on chip on one cluster of C = 1, 2, 4 or 8 CTAs (8192
+// keys each), keys exchanged through distributed shared memory between
+// rounds. A key >= 2^key_bits: ISORT_ERR_KEY_RANGE, buffers unchanged.
+isort_status radix_small_u32(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout, uint32_t n,
+                             int key_bits, cudaStream_t s) {
+    if (n == 0 || n > 8u * kSegChunk) return ISORT_ERR_INVALID_ARG;
+    SegCtl* ctl = nullptr;
+    ISORT_TRY(scratch_alloc((void**)&ctl, sizeof(SegCtl), s));
+    isort_status st = from_cuda(cudaMemsetAsync(ctl, 0, sizeof(SegCtl), s));
+    ClusterArgs a{};
+    a.keys = const_cast<uint32_t*>(kin);  // only read when kout is set
+    a.vals = const_cast<uint32_t*>(vin);
+    a.keys_out = kout;
+    a.vals_out = vout;
+    a.ctl = ctl;
+    a.key_bits = key_bits;
+    a.single_n = n;
+    const bool hv = vin != nullptr;
+    if (st == ISORT_OK) {
+        if (n <= (uint32_t)kSegChunk) st = launch_cluster_single<1>(hv, a, s);
+        else if (n <= 2u * kSegChunk) st = launch_cluster_single<2>(hv, a, s);
+        else if (n <= 4u * kSegChunk) st = launch_cluster_single<4>(hv, a, s);
+        else st = launch_cluster_single<8>(hv, a, s);
+    }
+    if (st == ISORT_OK) st = finish_status(&ctl->status, s);
+    scratch_free(ctl, s);
+    return st;
+}
+
 isort_status segmented_finish_u32(uint32_t* keys, uint32_t* vals, const uint64_t* off, uint32_t nseg,
                                   const uint32_t* seg_lo, const uint8_t* seg_bits, cudaStream_t s) {
     return segmented_entry(keys, vals, off, nseg, 32, (void*)s, seg_lo, seg_bits);
