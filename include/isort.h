@@ -86,6 +86,8 @@ ISORT_API const char* isort_status_string(isort_status s);
  * are that round's stable count-sort: a one-pass 2^16-way round would need
  * 2^16 counters per chunk, more than an SM's shared memory, and a one-pass
  * 2^11-way round measured slower than its two passes.
+ * Up to 65,536 u32 keys at radix 2^8 sort in one launch: one thread-block
+ * cluster (1, 2, 4 or 8 CTAs of 8,192 keys) runs every round on chip.
  * In place: on ISORT_OK keys (and vals) hold the sorted result.
  * ------------------------------------------------------------------------- */
 ISORT_API isort_status isort_radix(uint32_t* keys, uint32_t* vals, size_t n, int key_bits, int radix_bits, void* stream);
