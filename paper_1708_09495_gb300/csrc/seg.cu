@@ -416,8 +416,11 @@ __device__ __forceinline__ void btn_warp_fill(uint32_t* k, uint32_t* v, uint32_t
 // ib = bit_length(len) so that every item is below the pad 0xFFFFFFFF (keys
 // only: no index, ib = 0). Needs shift + ib <= 32, shift the bits the group's
 // keys span above gkb.
+// ks / vs: where the group is read (global memory, or the staging buffer in
+// shared memory); k / v: where the sorted group is written.
 template <int B, bool VALS, typename K>
-__device__ __forceinline__ void btn_warp_packed(K* k, uint32_t* v, uint32_t len, K gkb, int ib) {
+__device__ __forceinline__ void btn_warp_packed(const K* ks, const uint32_t* vs, K* k, uint32_t* v, uint32_t len,
+                                                K gkb, int ib) {
     const int t = threadIdx.x & 31;
     int p = 1;
     while ((uint32_t)(p * B) < len) p <<= 1;
@@ -425,7 +428,7 @@ __device__ __forceinline__ void btn_warp_packed(K* k, uint32_t* v, uint32_t len,
 #pragma unroll
     for (int i = 0; i < B; ++i) {
         const uint32_t g = (uint32_t)t * B + i;
-        x[i] = g < len ? (((k[g] - gkb) << ib) | (VALS ? (K)g : (K)0)) : ~(K)0;
+        x[i] = g < len ? (((ks[g] - gkb) << ib) | (VALS ? (K)g : (K)0)) : ~(K)0;
     }
     net::local_sort<B, K>(x);
     for (int kk = 2; kk <= p; kk <<= 1) {
@@ -442,7 +445,7 @@ __device__ __forceinline__ void btn_warp_packed(K* k, uint32_t* v, uint32_t len,
 #pragma unroll
         for (int i = 0; i < B; ++i) {
             const uint32_t g = (uint32_t)t * B + i;
-            vv[i] = g < len ? v[(uint32_t)(x[i] & m)] : 0u;
+            vv[i] = g < len ? vs[(uint32_t)(x[i] & m)] : 0u;
         }
     }
     __syncwarp();  // every payload is read before any is written
@@ -472,18 +475,29 @@ __device__ __forceinline__ bool group_warp_ok(uint32_t len, int shift) {
     return len <= (uint32_t)kSplitWarpMax && (sizeof(K) == 4 || group_packs<VALS, K>(len, shift));
 }
 
+// ks / vs: the group's source (by default the destination itself).
 template <bool VALS, typename K>
-__device__ __forceinline__ void finish_group_warp(K* k, uint32_t* v, uint32_t len, K gkb, int shift) {
+__device__ __forceinline__ void finish_group_warp(K* k, uint32_t* v, uint32_t len, K gkb, int shift,
+                                                  const K* ks = nullptr, const uint32_t* vs = nullptr) {
     const int ib = VALS ? 32 - __clz(len) : 0;
     if (group_packs<VALS, K>(len, shift)) {
-        if (len <= 32) btn_warp_packed<1, VALS, K>(k, v, len, gkb, ib);
-        else if (len <= 64) btn_warp_packed<2, VALS, K>(k, v, len, gkb, ib);
-        else if (len <= 128) btn_warp_packed<4, VALS, K>(k, v, len, gkb, ib);
-        else if (len <= 256) btn_warp_packed<8, VALS, K>(k, v, len, gkb, ib);
-        else btn_warp_packed<16, VALS, K>(k, v, len, gkb, ib);
+        const K* sk = ks ? ks : k;
+        const uint32_t* sv = ks ? vs : v;
+        if (len <= 32) btn_warp_packed<1, VALS, K>(sk, sv, k, v, len, gkb, ib);
+        else if (len <= 64) btn_warp_packed<2, VALS, K>(sk, sv, k, v, len, gkb, ib);
+        else if (len <= 128) btn_warp_packed<4, VALS, K>(sk, sv, k, v, len, gkb, ib);
+        else if (len <= 256) btn_warp_packed<8, VALS, K>(sk, sv, k, v, len, gkb, ib);
+        else btn_warp_packed<16, VALS, K>(sk, sv, k, v, len, gkb, ib);
         return;
     }
     if constexpr (sizeof(K) == 4) {
+        if (ks) {  // the 64-bit item networks sort in place: bring the group over first
+            for (uint32_t g = threadIdx.x & 31; g < len; g += 32) {
+                k[g] = ks[g];
+                if constexpr (VALS) v[g] = vs[g];
+            }
+            __syncwarp();
+        }
         if (len <= 32) btn_warp_fill<1>(k, v, len);
         else if (len <= 64) btn_warp_fill<2>(k, v, len);
         else if (len <= 128) btn_warp_fill<4>(k, v, len);
@@ -655,6 +669,12 @@ __global__ void __launch_bounds__(kSegThreads, (RB == 8 && sizeof(K) == 4) ? 2 :
             for (uint32_t j = tid; j < my_n; j += kSegThreads) {
                 const K key = s_keys[j];
                 const uint32_t dg = (uint32_t)((key - kb) >> shift) & (uint32_t)(BINS - 1);
+                if constexpr (C == 1) {
+                    // a group a warp finishes is written once, by that warp, from
+                    // this staging buffer
+                    const uint32_t len = s_start[dg + 1] - s_start[dg];
+                    if (shift > 0 && len > 1 && group_warp_ok<VALS, K>(len, shift)) continue;
+                }
                 const uint32_t o = s_base[dg] + (j - s_lst[dg]);
                 gk[o] = key;
                 if constexpr (VALS) gv[o] = s_vals[j];
@@ -666,7 +686,12 @@ __global__ void __launch_bounds__(kSegThreads, (RB == 8 && sizeof(K) == 4) ? 2 :
                 for (int d = (int)r * kSegWarps + warp; d < BINS; d += C * kSegWarps) {
                     const uint32_t c0 = s_start[d], c1 = s_start[d + 1], len = c1 - c0;
                     if (len <= 1 || !group_warp_ok<VALS, K>(len, shift)) continue;
-                    finish_group_warp<VALS, K>(gk + c0, VALS ? gv + c0 : nullptr, len, kb + ((K)d << shift), shift);
+                    if constexpr (C == 1)  // the whole group is in this CTA's staging buffer
+                        finish_group_warp<VALS, K>(gk + c0, VALS ? gv + c0 : nullptr, len, kb + ((K)d << shift), shift,
+                                                   s_keys + c0, VALS ? s_vals + c0 : nullptr);
+                    else
+                        finish_group_warp<VALS, K>(gk + c0, VALS ? gv + c0 : nullptr, len, kb + ((K)d << shift),
+                                                   shift);
                 }
                 if (warp == 0) {  // push the groups above a warp's reach, in digit order
                     uint32_t top2 = s_misc[2];
