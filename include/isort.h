@@ -214,7 +214,8 @@ ISORT_API isort_status isort_segmented(uint32_t* keys, uint32_t* vals, const uin
  * n < 2^18 sorts with the plain rounds. If more than half of the keys fall in
  * buckets beyond the on-chip capacity (65,536 keys) the call sorts with the
  * plain rounds instead (stats->fell_back_to_lsd = 1); fewer such buckets are
- * sorted by the plain rounds one at a time. The call synchronizes
+ * gathered into one buffer (their key ranges are disjoint and ordered), sorted
+ * by one call of the plain rounds and scattered back. The call synchronizes
  * (the bucket sizes are read on the host). stats (host, may be NULL) receives
  * the bucket balance and the training record.
  * ------------------------------------------------------------------------- */

@@ -355,6 +355,41 @@ __global__ void __launch_bounds__(kFitThreads, 1)
     }
 }
 
+// ---------------------------------------------------------------- overflow buckets
+
+// Moves nr ranges between the array (keys, vals) and a packed copy (pk, pv):
+// range r is [off[r], off[r] + len_r) in the array and [pos[r], pos[r + 1])
+// in the copy; chunk c (kMoveChunk elements) of the launch belongs to range r
+// with cstart[r] <= c < cstart[r + 1]. gather: array -> copy; else copy -> array.
+constexpr uint32_t kMoveChunk = 4096;
+
+template <typename K>
+__global__ void k_move_ranges(K* keys, uint32_t* vals, K* pk, uint32_t* pv, const uint64_t* __restrict__ off,
+                              const uint64_t* __restrict__ pos, const uint32_t* __restrict__ cstart, uint32_t nr,
+                              int gather) {
+    const uint32_t c = blockIdx.x;
+    uint32_t lo = 0, hi = nr;  // the last r with cstart[r] <= c
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) / 2;
+        if (cstart[mid] <= c) lo = mid;
+        else hi = mid;
+    }
+    const uint32_t r = lo;
+    const uint64_t len = pos[r + 1] - pos[r];
+    const uint64_t e0 = (uint64_t)(c - cstart[r]) * kMoveChunk;
+    const uint64_t e1 = min(len, e0 + kMoveChunk);
+    for (uint64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const uint64_t a = off[r] + e, p = pos[r] + e;
+        if (gather) {
+            pk[p] = keys[a];
+            if (vals) pv[p] = vals[a];
+        } else {
+            keys[a] = pk[p];
+            if (vals) vals[a] = pv[p];
+        }
+    }
+}
+
 // ---------------------------------------------------------------- splitters
 
 // s_0 = 0; s_b = the first key whose bucket is at least b (the largest key if
@@ -852,9 +887,48 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(segbits, h_bits.data(), (size_t)B, cudaMemcpyHostToDevice, s);
     if (ce != cudaSuccess) return fail(from_cuda(ce));
     st = finish_buckets(keys, vals, segoff, (uint32_t)B, seglo, segbits, s);
-    for (size_t i = 0; i < big.size() && st == ISORT_OK; ++i) {
-        const int b = big[i];
+    if (st == ISORT_OK && big.size() == 1) {
+        const int b = big[0];
         st = plain_sort(keys + h_off[b], hv ? vals + h_off[b] : nullptr, h_count[b], key_bits, s);
+    } else if (st == ISORT_OK && big.size() > 1) {
+        // The overflow buckets hold disjoint key ranges in increasing order, so
+        // their concatenation (in bucket order) sorted stably is each of them
+        // sorted: gather them into the free distribution buffer, sort that
+        // once with the plain rounds, scatter back.
+        const uint32_t nr = (uint32_t)big.size();
+        std::vector<uint64_t> h_roff(nr), h_pos(nr + 1);
+        std::vector<uint32_t> h_cst(nr + 1);
+        h_pos[0] = 0;
+        h_cst[0] = 0;
+        for (uint32_t r = 0; r < nr; ++r) {
+            h_roff[r] = h_off[big[r]];
+            h_pos[r + 1] = h_pos[r] + h_count[big[r]];
+            h_cst[r + 1] = h_cst[r] + (uint32_t)((h_count[big[r]] + kMoveChunk - 1) / kMoveChunk);
+        }
+        unsigned char* tab = nullptr;
+        const size_t tb8 = align_up((size_t)(nr + 1) * 8, 256);
+        st = scratch_alloc((void**)&tab, 3 * tb8, s);
+        if (st == ISORT_OK) {
+            uint64_t* d_roff = reinterpret_cast<uint64_t*>(tab);
+            uint64_t* d_pos = reinterpret_cast<uint64_t*>(tab + tb8);
+            uint32_t* d_cst = reinterpret_cast<uint32_t*>(tab + 2 * tb8);
+            ce = cudaMemcpyAsync(d_roff, h_roff.data(), (size_t)nr * 8, cudaMemcpyHostToDevice, s);
+            if (ce == cudaSuccess) ce = cudaMemcpyAsync(d_pos, h_pos.data(), (size_t)(nr + 1) * 8, cudaMemcpyHostToDevice, s);
+            if (ce == cudaSuccess) ce = cudaMemcpyAsync(d_cst, h_cst.data(), (size_t)(nr + 1) * 4, cudaMemcpyHostToDevice, s);
+            if (ce == cudaSuccess) {
+                LaunchScope ls("overflow_gather", s);
+                k_move_ranges<K><<<h_cst[nr], 256, 0, s>>>(keys, vals, wk, wv, d_roff, d_pos, d_cst, nr, 1);
+                ce = cudaGetLastError();
+            }
+            st = from_cuda(ce);
+            if (st == ISORT_OK) st = plain_sort(wk, wv, h_pos[nr], key_bits, s);
+            if (st == ISORT_OK) {
+                LaunchScope ls("overflow_scatter", s);
+                k_move_ranges<K><<<h_cst[nr], 256, 0, s>>>(keys, vals, wk, wv, d_roff, d_pos, d_cst, nr, 0);
+                st = from_cuda(cudaGetLastError());
+            }
+            scratch_free(tab, s);
+        }
     }
     if (st != ISORT_OK) return fail(st);
     st = finish_status(status, s);

@@ -153,6 +153,20 @@ def test_learned_heavy_buckets_finish_by_plain_rounds(cuda_lib):
     assert not st["fell_back_to_lsd"]
 
 
+def test_learned_overflow_buckets_apart_are_sorted_together(cuda_lib):
+    """Two narrow bands far apart, each a fifth of the keys: several buckets
+    over the on-chip capacity in separate places, gathered, sorted by one call
+    of the plain rounds and scattered back (payload = index checks stability)."""
+    n = (1 << 21) + 77
+    keys = gen.uniform_u32(n, 32, 21, 0)
+    band = gen.uniform_u32(n, 12, 21, 1)
+    keys[: n // 5] = (100_000_000 + band[: n // 5]).astype(np.uint32)
+    keys[n // 5: 2 * n // 5] = (3_000_000_000 + band[n // 5: 2 * n // 5]).astype(np.uint32)
+    st = _learned_vs_oracle(cuda_lib, keys)
+    assert st["overflow_buckets"] >= 2 and not st["fell_back_to_lsd"]
+    _learned_vs_oracle(cuda_lib, keys, vals=False)
+
+
 def test_learned_rejects(cuda_lib):
     import torch
 
