@@ -25,7 +25,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-E2E_SLOTS = 3  # e2e: streams (and host output buffers) in flight
+E2E_SLOTS = 4  # e2e: streams (and host output buffers) in flight
 MODELS = {0: "piecewise-linear CDF", 1: "1-32-1 MLP CDF", 2: "regular sampling, no trained model"}
 METRIC = "Gkeys/s (u32 n=2^28) & % HBM roofline; learned/batched vs plain LSD, bit-exact"
 UNIT = "Gkeys/s"
@@ -291,12 +291,13 @@ def run_ours(args):
         # are collected after it.
         hk = torch.from_numpy(keys.view(np.int32)).pin_memory()
         hv = torch.from_numpy(vals.view(np.int32)).pin_memory()
-        hko = [torch.empty_like(hk).pin_memory() for _ in range(E2E_SLOTS)]
-        hvo = [torch.empty_like(hv).pin_memory() for _ in range(E2E_SLOTS)]
-        e2e_streams = [torch.cuda.Stream() for _ in range(E2E_SLOTS)]
+        slots = max(1, args.e2e_slots)
+        hko = [torch.empty_like(hk).pin_memory() for _ in range(slots)]
+        hvo = [torch.empty_like(hv).pin_memory() for _ in range(slots)]
+        e2e_streams = [torch.cuda.Stream() for _ in range(slots)]
 
         def e2e_step(i):
-            j = i % E2E_SLOTS
+            j = i % slots
             rc = lib.isort_radix_copy(ctypes.c_void_p(hk.data_ptr()), ctypes.c_void_p(hv.data_ptr()),
                                       ctypes.c_void_p(hko[j].data_ptr()), ctypes.c_void_p(hvo[j].data_ptr()), N,
                                       KEY_BITS, RADIX_BITS, ctypes.c_void_p(e2e_streams[j].cuda_stream))
@@ -305,10 +306,10 @@ def run_ours(args):
 
         lib.isort_set_sync(0)
         try:
-            for i in range(E2E_SLOTS):
+            for i in range(slots):
                 e2e_step(i)
             torch.cuda.synchronize()
-            e2e_steps = max(E2E_SLOTS, min(args.steps, 3 * E2E_SLOTS))
+            e2e_steps = max(slots, min(args.steps, 3 * slots))
             barrier()
             t0 = time.perf_counter()
             for i in range(e2e_steps):
@@ -321,13 +322,13 @@ def run_ours(args):
         rc = lib.isort_device_status(1, None)
         if rc != 0:
             raise RuntimeError(f"e2e device status: {isort.STATUS.get(rc, rc)}")
-        last = (e2e_steps - 1) % E2E_SLOTS
+        last = (e2e_steps - 1) % slots
         ko = hko[last].numpy().view(np.uint32)
         if not bool(np.all(ko[1:] >= ko[:-1])):
             raise RuntimeError("e2e output not sorted")
         e2e = {"value": world * e2e_steps * N / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": N * 8,
                "d2h_bytes_per_step": N * 8, "steps": e2e_steps,
-               "how": f"isort_radix_copy host->host, {E2E_SLOTS} streams in flight (asynchronous status mode)"}
+               "how": f"isort_radix_copy host->host, {slots} streams in flight (asynchronous status mode)"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -608,6 +609,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-slots", type=int, default=E2E_SLOTS, help="e2e: calls (streams) in flight")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--log2n", type=int, default=28)
     ap.add_argument("--radix-bits", type=int, default=8)

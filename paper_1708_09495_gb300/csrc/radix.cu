@@ -56,6 +56,7 @@ static Tune load_tune() {
         else if (!strcmp(key, "sweep8")) t.sweep_small = val;
         else if (!strcmp(key, "sweep11")) t.sweep_large = val;
         else if (!strcmp(key, "split")) t.split = val;
+        else if (!strcmp(key, "copy_pieces")) t.copy_pieces = val;
         else if (!strcmp(key, "small")) t.small = val;
         p += used;
         if (*p == ',') ++p;
@@ -1052,8 +1053,11 @@ struct CopyStreams {
 thread_local std::map<std::pair<int, cudaStream_t>, CopyStreams> t_copy;
 
 cudaError_t copy_split(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    // pieces help a call that runs alone; with calls in flight on several
+    // streams (the asynchronous status mode) one copy per buffer is faster
     const size_t piece_min = size_t(64) << 20;
-    const int pieces = (int)std::min<size_t>(kCopyStreams, std::max<size_t>(1, bytes / piece_min));
+    const int max_pieces = sync_mode() ? std::min(kCopyStreams, tune().copy_pieces) : 1;
+    const int pieces = (int)std::min<size_t>(max_pieces, std::max<size_t>(1, bytes / piece_min));
     if (pieces <= 1) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s);
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);

@@ -15,7 +15,8 @@ struct Tune {
     int sweep_small = 4;  // chunked-round launch shape, digits of <= 8 bits (4: half-warp ranking)
     int sweep_large = 2;  // chunked-round launch shape, wider digits
     int small = 1;        // u32 sorts of <= 65,536 keys in place at radix 2^8: one on-chip cluster launch
-    int split = 8;        // chunked rounds: a digit wider than this runs as two stable passes (8..16)
+    int split = 8;
+    int copy_pieces = 4;  // host-buffer staging copies: at most this many pieces on auxiliary streams        // chunked rounds: a digit wider than this runs as two stable passes (8..16)
 };
 
 const Tune& tune();
