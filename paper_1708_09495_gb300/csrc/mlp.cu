@@ -42,6 +42,8 @@ namespace {
 __device__ __forceinline__ float mlp_softplus(float t) { return t > 20.f ? t : log1pf(expf(t)); }
 __device__ __forceinline__ float mlp_inv_softplus(float v) { return v > 20.f ? v : logf(expm1f(v)); }
 __device__ __forceinline__ float mlp_sigmoid(float t) { return 1.f / (1.f + expf(-t)); }
+// The fit's sigmoid on the fast exponential and division (the table keeps mlp_sigmoid).
+__device__ __forceinline__ float mlp_sigmoid_fast(float t) { return __fdividef(1.f, 1.f + __expf(-t)); }
 
 __device__ __forceinline__ float mlp_warp_total(float v) {
 #pragma unroll
@@ -115,10 +117,11 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
     const float inv_m = 1.f / (float)m;
     float best_loss = INFINITY, first = 0.f;
     const float be1 = 0.9f, be2 = 0.999f;
+    float pw1 = 1.f, pw2 = 1.f;  // be1^(step + 1), be2^(step + 1) after the update below
     for (int step = 0;; ++step) {
         const int buf = step & 1;
         const float w1 = mlp_softplus(th[lane]), b1 = th[kMlpUnits + lane], w2 = mlp_softplus(th[2 * kMlpUnits + lane]);
-        const float h0 = mlp_sigmoid(b1), h1 = mlp_sigmoid(fmaf(w1, 1.f, b1));
+        const float h0 = mlp_sigmoid_fast(b1), h1 = mlp_sigmoid_fast(fmaf(w1, 1.f, b1));
         const float inv_D = 1.f / mlp_warp_total(w2 * (h1 - h0));
         float A = 0.f, Bs = 0.f, Cs = 0.f, loss = 0.f, c0 = 0.f, c1 = 0.f;
         for (uint32_t base = i0 + warp; base < i1; base += 4 * kMlpWarps) {
@@ -130,7 +133,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                h[q] = mlp_sigmoid(fmaf(w1, x[q], b1));
+                h[q] = mlp_sigmoid_fast(fmaf(w1, x[q], b1));
                 z[q] = w2 * (h[q] - h0);
             }
 #pragma unroll
@@ -200,12 +203,13 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
             if (t == kMlpTrained) grad_out[t] = 0.f;
         }
         if (step == steps) break;
+        pw1 *= be1;
+        pw2 *= be2;
         if (t < kMlpTrained) {
             const float d = g[t];
             const float a = mo1[t] = be1 * mo1[t] + (1.f - be1) * d;
             const float v = mo2[t] = be2 * mo2[t] + (1.f - be2) * d * d;
-            const float k1 = 1.f - powf(be1, (float)(step + 1)), k2 = 1.f - powf(be2, (float)(step + 1));
-            th[t] -= lr * (a / k1) / (sqrtf(v / k2) + 1e-8f);
+            th[t] -= lr * (a / (1.f - pw1)) / (sqrtf(v / (1.f - pw2)) + 1e-8f);
         }
         __syncthreads();
     }
