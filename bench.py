@@ -25,7 +25,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-E2E_SLOTS = 4  # e2e: streams (and host output buffers) in flight
+E2E_SLOTS = 3  # e2e: streams (and host output buffers) in flight
 MODELS = {0: "piecewise-linear CDF", 1: "1-32-1 MLP CDF", 2: "regular sampling, no trained model"}
 METRIC = "Gkeys/s (u32 n=2^28) & % HBM roofline; learned/batched vs plain LSD, bit-exact"
 UNIT = "Gkeys/s"
