@@ -390,6 +390,8 @@ def run_compare(args):
     segmented: the log-uniform-length segment batch (2^28 keys, payload),
              batched segmented sort vs one plain LSD of composite u64 keys
              (segment id << 32 | key).
+    typed: 2^log2n float32 keys + payload in IEEE totalOrder vs the same bits
+             sorted as u32 keys.
     Inputs are restored from a pristine copy before every step (not timed)."""
     import numpy as np
     import torch
@@ -499,6 +501,52 @@ def run_compare(args):
                           "call": f"isort_radix_u64, radix 2^8, {bits // 8} rounds, in place"},
             "speedup_vs_plain": ms_p / ms_l,
             "learned_stats": st.as_dict(),
+            "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in prof.items()},
+        })
+    elif args.workload == "typed":
+        # 2^log2n float32 keys (normal, every magnitude and sign, with -0.0) + u32 payload = index, sorted in
+        # IEEE totalOrder, against the same bits sorted as u32 keys by the plain rounds
+        n = 1 << args.log2n
+        r = np.random.default_rng(7)
+        keys = (r.standard_normal(n, dtype=np.float32) * np.float32(1e3)).astype(np.float32)
+        keys[::1021] = -0.0
+        vals = np.arange(n, dtype=np.uint32)
+        kin = torch.from_numpy(keys.view(np.int32)).cuda()
+        vin = torch.from_numpy(vals.view(np.int32)).cuda()
+        kw, vw = torch.empty_like(kin), torch.empty_like(vin)
+
+        def typed():
+            rc = lib.isort_radix_typed(ctypes.c_void_p(kw.data_ptr()), 2, ctypes.c_void_p(vw.data_ptr()), n,
+                                       args.radix_bits, sp)
+            if rc != 0:
+                raise RuntimeError(f"isort_radix_typed: {isort.STATUS.get(rc, rc)}")
+
+        def plain():
+            rc = lib.isort_radix(ctypes.c_void_p(kw.data_ptr()), ctypes.c_void_p(vw.data_ptr()), n, 32,
+                                 args.radix_bits, sp)
+            if rc != 0:
+                raise RuntimeError(f"isort_radix: {isort.STATUS.get(rc, rc)}")
+
+        def reset():
+            kw.copy_(kin)
+            vw.copy_(vin)
+
+        isort.profile_read()
+        isort.profile_enable(True)
+        ms_t = _timed_inplace(typed, reset, args.steps, args.warmup, stream)
+        isort.profile_enable(False)
+        prof = isort.profile_read()
+        sk = kw.view(torch.float32)[:: max(1, n // 65536)].cpu().numpy()
+        if not np.all(sk[1:] >= sk[:-1]):
+            raise RuntimeError("typed output not sorted")
+        ms_p = _timed_inplace(plain, reset, args.steps, args.warmup, stream)
+        line.update({
+            "value": args.steps * n / (ms_t * 1e-3) / 1e9, "ms_per_step": ms_t / args.steps, "dtype": "f32",
+            "config": {"workload": f"typed keys: float32 normal(0, 1e3) with -0.0 (seed 7) + u32 payload = index, "
+                                   f"IEEE totalOrder, n = 2^{args.log2n}, radix 2^{args.radix_bits}",
+                       "l2": "inputs larger than L2; restored before each step (untimed)"},
+            "plain_lsd": {"value": args.steps * n / (ms_p * 1e-3) / 1e9, "ms_per_step": ms_p / args.steps,
+                          "call": f"isort_radix on the same bits as u32 keys, radix 2^{args.radix_bits}"},
             "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in prof.items()},
         })
     elif args.workload == "learned":
@@ -613,7 +661,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--log2n", type=int, default=28)
     ap.add_argument("--radix-bits", type=int, default=8)
-    ap.add_argument("--workload", default="uniform", choices=["uniform", "learned", "learned64", "segmented", "small"],
+    ap.add_argument("--workload", default="uniform",
+                    choices=["uniform", "learned", "learned64", "segmented", "small", "typed"],
                     help="uniform: the benchmark; learned / segmented: secondary comparisons with plain LSD; "
                          "small: the 65,536-key case and the block networks on 1,024 keys")
     ap.add_argument("--nbuckets", type=int, default=0, help="learned: bucket count (0: the library's choice)")
