@@ -73,6 +73,18 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.isort_btn_p(None, None, 1 << 20, 1024, None, None) == 6
     assert lib.isort_set_spin_limit(0) == 1
     assert lib.isort_count_round(None, None, None, None, 10, 30, 8, None) == 1
+    # typed keys: key type, digit width and buffers are checked first
+    assert lib.isort_radix_typed(None, 7, None, 100, 8, None) == 1
+    assert lib.isort_radix_typed(None, 2, None, 100, 17, None) == 1
+    assert lib.isort_radix_typed(None, 2, None, 100, 8, None) == 1
+    assert lib.isort_radix_typed(None, 2, None, 1, 8, None) == 0
+    # learned sort: bucket count and model are checked first
+    assert lib.isort_learned(None, None, 100, 0, 1, 0, None, None) == 1
+    assert lib.isort_learned(None, None, 100, 0, 65536, 0, None, None) == 1
+    assert lib.isort_learned(None, None, 100, 0, 0, 3, None, None) == 1
+    # the MLP model's entry points
+    assert lib.isort_mlp_loss_grad(None, 10, None, None, None, None) == 1
+    assert lib.isort_mlp_train(None, 1, 32, None, None, None, None, None) == 1
 
 
 def test_graft_entry_build_is_importable():
