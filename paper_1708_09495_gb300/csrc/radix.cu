@@ -61,7 +61,7 @@ static Tune load_tune() {
         p += used;
         if (*p == ',') ++p;
     }
-    if (t.sweep_small < 0 || t.sweep_small >= 5) t.sweep_small = 4;
+    if (t.sweep_small < 0 || t.sweep_small >= 6) t.sweep_small = 4;
     if (t.sweep_large < 0 || t.sweep_large >= 4) t.sweep_large = 2;
     if (t.split < 8 || t.split > 16) t.split = 8;
     auto built = [](int sh) { return sh == 0 || sh == 1 || sh == 4 || sh == 9 || sh == 10; };

@@ -13,6 +13,7 @@
 #include "runtime.h"
 #include "sweep.cuh"
 #include "tune.h"
+#include "wrank.cuh"
 
 namespace isort {
 
@@ -26,8 +27,11 @@ namespace {
 // shapes 0-3: the generic chunked round; 4: the half-warp ranking variant (u32
 // keys and 8-bit digits; other cases take the generic round of the same tile).
 // Half-warp shapes 256 x 16 and 512 x 16 measured slower and are not built.
-constexpr int kSweepThreads[] = {256, 512, 256, 512, 512};
-constexpr int kSweepItems[] = {16, 16, 8, 8, 8};
+// 5: the warp-ranked round (wrank.cuh; u32 keys and digits of up to 8 bits;
+// other cases take shape 4).
+constexpr int kSweepThreads[] = {256, 512, 256, 512, 512, 512};
+constexpr int kSweepItems[] = {16, 16, 8, 8, 8, 8};
+constexpr int kNumShapes = (int)(sizeof(kSweepThreads) / sizeof(kSweepThreads[0]));
 
 int sweep_tile(int sh) { return kSweepThreads[sh] * kSweepItems[sh]; }
 
@@ -99,9 +103,29 @@ isort_status sweep_hw_or_generic(bool occupancy_only, int bins, int* per_sm, con
     return launch_sweep<K, VALS, THREADS, ITEMS>(*a, chunks, s);
 }
 
+// The pipelined warp-ranked round (u32 keys, digits of up to 8 bits).
+template <bool VALS, int THREADS, int ITEMS, int MINB>
+isort_status sweep_wp(bool occupancy_only, int* per_sm, const SweepArgs* a, uint32_t chunks, cudaStream_t s) {
+    using Cfg = WpCfg<VALS, THREADS, ITEMS>;
+    const size_t smem = Cfg::smem_bytes();
+    if (smem > max_smem_optin()) return ISORT_ERR_UNSUPPORTED;
+    auto kern = k_downsweep_wp<VALS, THREADS, ITEMS, MINB>;
+    ISORT_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (occupancy_only) {
+        ISORT_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, THREADS, smem));
+        return *per_sm >= 1 ? ISORT_OK : ISORT_ERR_UNSUPPORTED;
+    }
+    LaunchScope ls("downsweep", s);
+    kern<<<chunks, THREADS, smem, s>>>(*a);
+    return from_cuda(cudaGetLastError());
+}
+
 template <typename K, bool VALS>
 isort_status sweep_dispatch(int sh, bool occupancy_only, int bins, int* per_sm, const SweepArgs* a, uint32_t chunks,
                             cudaStream_t s) {
+    if constexpr (sizeof(K) == 4) {
+        if (sh == 5) return sweep_wp<VALS, 512, 8, 2>(occupancy_only, per_sm, a, chunks, s);
+    }
     switch (sh) {
         case 0:
             return occupancy_only ? sweep_occupancy<K, VALS, 256, 16>(bins, per_sm)
@@ -178,7 +202,7 @@ int autotuned_shape(const K* kin, bool vals, size_t n, int key_bits, int rb, cud
     const auto it = as.shapes.find(key);
     if (it != as.shapes.end()) return it->second;
 
-    std::vector<int> cands = bins <= 256 ? std::vector<int>{4, 3, 1} : std::vector<int>{2, 0};
+    std::vector<int> cands = bins <= 256 ? std::vector<int>{4, 5, 3, 1} : std::vector<int>{2, 0};
     const size_t m = size_t(1) << log2n;
     const size_t kb = align_up(m * sizeof(K), 256);
     unsigned char* buf = nullptr;
@@ -258,7 +282,8 @@ isort_status radix_device_rts(const K* kin, const uint32_t* vin, K* kout, uint32
     const int bins = 1 << max_width;
     const bool vals = vin != nullptr;
     const bool inplace = (const void*)kin == (const void*)kout;
-    const int sh = shape >= 0 ? shape : autotuned_shape<K>(kin, vals, n, key_bits, max_width, s);
+    int sh = shape >= 0 ? shape : autotuned_shape<K>(kin, vals, n, key_bits, max_width, s);
+    if (sh == 5 && (sizeof(K) != 4 || bins > kWrBins)) sh = bins <= 256 ? 4 : 2;  // warp-ranked: u32, <= 8 bits
     int per_sm = 0;
     isort_status st = vals ? sweep_dispatch<K, true>(sh, true, bins, &per_sm, nullptr, 0, s)
                            : sweep_dispatch<K, false>(sh, true, bins, &per_sm, nullptr, 0, s);
@@ -324,10 +349,15 @@ isort_status radix_device_rts(const K* kin, const uint32_t* vin, K* kout, uint32
         const int shift = pass_shift[d];
         const int width = pass_width[d];
         {
+            // several CTAs per chunk when chunks are fewer than two per SM
+            const int parts = std::max(1, (2 * sm_count() + (int)chunks - 1) / (int)chunks);
+            if (parts > 1) {
+                ce = cudaMemsetAsync(hist, 0, (size_t)chunks * (1u << width) * 4, s);
+                if (ce != cudaSuccess) return fail(from_cuda(ce));
+            }
             LaunchScope ls("chunk_hist", s);
-            k_chunk_hist<K><<<chunks, kChunkHistThreads, hist_smem, s>>>(src_k, (uint32_t)n, shift, width,
-                                                                         chunk_tiles * tile, nsub, hist,
-                                                                         d == 0 ? key_or : nullptr);
+            k_chunk_hist<K><<<chunks * parts, kChunkHistThreads, hist_smem, s>>>(
+                src_k, (uint32_t)n, shift, width, chunk_tiles * tile, nsub, hist, d == 0 ? key_or : nullptr, parts);
             ce = cudaGetLastError();
             if (ce != cudaSuccess) return fail(from_cuda(ce));
         }
@@ -397,8 +427,7 @@ isort_status isort_autotune(int enable, const char* cache_path) {
             AutoKey k;
             int shape = 0;
             while (std::fscanf(f, "%d %d %d %d %d", &k.key_bytes, &k.vals, &k.wide, &k.log2n, &shape) == 5) {
-                const int nshapes = (int)(sizeof(kSweepThreads) / sizeof(kSweepThreads[0]));
-                if (shape >= 0 && shape < nshapes) as.shapes[k] = shape;
+                if (shape >= 0 && shape < kNumShapes) as.shapes[k] = shape;
             }
             std::fclose(f);
         }

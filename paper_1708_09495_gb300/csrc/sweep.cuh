@@ -76,11 +76,13 @@ __device__ void block_exclusive_scan(uint32_t* data, int count, uint32_t* s_warp
 // ----------------------------------------------------------------------------
 constexpr int kChunkHistThreads = 512;
 
+// parts CTAs share a chunk (each counts a contiguous part of it and adds its
+// counts to the chunk's row, which starts zeroed); parts == 1 stores the row.
 template <typename K>
 __global__ void __launch_bounds__(kChunkHistThreads) k_chunk_hist(const K* __restrict__ keys, uint32_t n, int shift,
                                                                   int width, uint32_t chunk_keys, int nsub,
                                                                   uint32_t* __restrict__ hist,
-                                                                  unsigned long long* key_or) {
+                                                                  unsigned long long* key_or, int parts = 1) {
     extern __shared__ __align__(16) uint32_t s_h[];  // [nsub][bins]
     const int bins = 1 << width;
     const uint32_t mask = (uint32_t)bins - 1u;
@@ -88,8 +90,11 @@ __global__ void __launch_bounds__(kChunkHistThreads) k_chunk_hist(const K* __res
     for (int i = tid; i < nsub * bins; i += kChunkHistThreads) s_h[i] = 0;
     __syncthreads();
     uint32_t* my = s_h + (size_t)((tid >> 5) % nsub) * bins;
-    const uint32_t lo = blockIdx.x * chunk_keys;
-    const uint32_t hi = min(n, lo + chunk_keys);
+    const uint32_t chunk = blockIdx.x / (uint32_t)parts, part = blockIdx.x % (uint32_t)parts;
+    const uint32_t part_keys = (chunk_keys / (uint32_t)parts + 3u) & ~3u;  // parts start 16-byte aligned
+    const uint32_t c_lo = chunk * chunk_keys, c_hi = min(n, c_lo + chunk_keys);
+    const uint32_t lo = min(c_hi, c_lo + part * part_keys);
+    const uint32_t hi = part + 1 == (uint32_t)parts ? c_hi : min(c_hi, lo + part_keys);
     K acc = 0;
     if (lo < hi) {
         const K* base = keys + lo;
@@ -124,11 +129,12 @@ __global__ void __launch_bounds__(kChunkHistThreads) k_chunk_hist(const K* __res
         }
     }
     __syncthreads();
-    uint32_t* out = hist + (size_t)blockIdx.x * bins;
+    uint32_t* out = hist + (size_t)chunk * bins;
     for (int d = tid; d < bins; d += kChunkHistThreads) {
         uint32_t sum = 0;
         for (int q = 0; q < nsub; ++q) sum += s_h[q * bins + d];
-        out[d] = sum;
+        if (parts == 1) out[d] = sum;
+        else if (sum) atomicAdd(&out[d], sum);
     }
     if (key_or) {
         const unsigned long long o = (unsigned long long)acc;
