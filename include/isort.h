@@ -306,7 +306,10 @@ ISORT_API isort_status isort_mlp_loss_grad(const float* u, uint32_t m, const flo
  * it keeps the last call's contents: calls whose work overlaps on the GPU
  * (different streams, or several calls enqueued in the asynchronous status
  * mode before the earlier ones finished) race and corrupt each other's
- * results.
+ * results. In the synchronous status mode the call waits for `stream` and
+ * returns device-detected errors, except while `stream` is being captured:
+ * then it returns after enqueueing and device-detected errors are recorded
+ * as in the asynchronous mode (read them with isort_device_status).
  * ------------------------------------------------------------------------- */
 ISORT_API isort_status isort_radix_noalloc(uint32_t* keys, uint32_t* vals, size_t n, int key_bits, int radix_bits,
                                            void* stream);

@@ -87,14 +87,17 @@ isort_status isort_radix_noalloc(uint32_t* keys, uint32_t* vals, size_t n, int k
     st = radix_u32_inplace_in_workspace(keys, vals, n, key_bits, radix_bits, ws, kNoAllocScratchBytes, s, &d_status);
     if (st != ISORT_OK) return st;
     if (!sync_mode()) return finish_status(d_status, s);  // folds into the device's sticky status; no allocation
-    // synchronous mode: read the status word into this stack variable
+    // A stream that is being captured cannot be waited for: the device status
+    // is then folded into the sticky word, as in the asynchronous mode.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    ISORT_TRY_CUDA(cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return fold_status(d_status, s);
+    // synchronous mode: read the status word into this stack variable and map
+    // it as isort_radix does
     uint32_t h = 0;
     ISORT_TRY_CUDA(cudaMemcpyAsync(&h, d_status, sizeof(h), cudaMemcpyDeviceToHost, s));
     ISORT_TRY_CUDA(cudaStreamSynchronize(s));
-    if (h & kStatTimeout) return ISORT_ERR_TIMEOUT;
-    if (h & kStatKeyRange) return ISORT_ERR_KEY_RANGE;
-    if (h) return ISORT_ERR_CUDA;
-    return ISORT_OK;
+    return map_bits(h);
 }
 
 }  // extern "C"

@@ -142,12 +142,14 @@ isort_status map_bits(uint32_t v) {
     return ISORT_OK;
 }
 
+isort_status fold_status(const uint32_t* d_status, cudaStream_t s) {
+    LaunchScope ls("fold_status", s);
+    k_fold_status<<<1, 32, 0, s>>>(d_status);
+    return from_cuda(cudaGetLastError());
+}
+
 isort_status finish_status(const uint32_t* d_status, cudaStream_t s) {
-    if (!sync_mode()) {
-        LaunchScope ls("fold_status", s);
-        k_fold_status<<<1, 32, 0, s>>>(d_status);
-        return from_cuda(cudaGetLastError());
-    }
+    if (!sync_mode()) return fold_status(d_status, s);
     static thread_local uint32_t* host_slot = nullptr;
     if (!host_slot) {
         if (cudaHostAlloc((void**)&host_slot, 64, cudaHostAllocDefault) != cudaSuccess) {

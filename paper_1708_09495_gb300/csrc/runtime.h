@@ -28,6 +28,10 @@ isort_status finish_status(const uint32_t* d_status, cudaStream_t s);
 // ISORT_TRACE=1 in the environment: launches are named on stderr and waited for.
 bool trace_on();
 
+// Folds a call's device status word into the device's sticky status word
+// (what the asynchronous status mode does), whatever the mode.
+isort_status fold_status(const uint32_t* d_status, cudaStream_t s);
+
 // The status of a device status word already read on the host.
 isort_status map_bits(uint32_t v);
 
