@@ -60,6 +60,8 @@ def _lib(mutant: int = 0):
             h.oracle_btn_u32.argtypes = [vp, vp, sz, i32, vp]
             h.oracle_oet_u32.argtypes = [vp, vp, sz, i32, vp]
             h.oracle_segmented_u32.argtypes = [vp, vp, vp, sz, i32, i32]
+            for nm in ("oracle_partition_u32", "oracle_partition_u64"):
+                getattr(h, nm).argtypes = [vp, vp, vp, vp, sz, vp, sz, i32, vp]
             for nm in ("oracle_is_sorted_u32", "oracle_is_sorted_u64"):
                 getattr(h, nm).argtypes = [vp, sz]
             for nm in ("oracle_is_stable_u32", "oracle_is_stable_u64"):
@@ -176,6 +178,23 @@ def segmented(keys, vals, offsets, key_bits: int = 0, radix_bits: int = 8):
     if rc != 0:
         raise ValueError("oracle_segmented: invalid arguments")
     return k, v
+
+
+def partition(keys, vals, sorted_sample, parts: int, mutant: int = 0):
+    """Sample-sort routing: splitter j = sorted_sample[floor(j m / parts)]
+    (1 <= j < parts), range of a key = number of splitters <= key, keys routed
+    stably by range. Returns (keys, vals, counts)."""
+    k = np.ascontiguousarray(keys)
+    v = None if vals is None else np.ascontiguousarray(vals, dtype=np.uint32)
+    smp = np.ascontiguousarray(sorted_sample, dtype=k.dtype)
+    ko = np.empty_like(k)
+    vo = None if v is None else np.empty_like(v)
+    counts = np.zeros(max(parts, 1), np.uint64)
+    rc = getattr(_lib(mutant), f"oracle_partition_{_kind(k)}")(_p(k), _p(v), _p(ko), _p(vo), k.size, _p(smp),
+                                                                 smp.size, parts, _p(counts))
+    if rc != 0:
+        raise ValueError("oracle_partition: invalid arguments")
+    return ko, vo, counts
 
 
 def is_sorted(keys) -> bool:

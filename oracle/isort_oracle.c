@@ -28,6 +28,12 @@
  *   oracle_insertion_*    brute force: stable insertion sort (a pin, not the
  *                         paper's method)
  *   oracle_segmented_u32  the LSD sort applied to each CSR segment on its own
+ *   oracle_partition_*    the routing step of a sample sort across p processors:
+ *                         splitters chosen regularly from a sorted sample
+ *                         (Section 2, the sample sorts with regular sampling),
+ *                         every key routed to the range of its splitters by one
+ *                         count-sort round on that range (Section 3, eq. Tp's
+ *                         key routing)
  *   invariant checkers    non-decreasing, stability (payload = index), 64-bit
  *                         commutative multiset hash
  *
@@ -123,6 +129,46 @@ DEFINE_COUNT_ROUND(oracle_count_round_u64, uint64_t)
 
 DEFINE_LSD(oracle_lsd_u32, oracle_count_round_u32, uint32_t, 32)
 DEFINE_LSD(oracle_lsd_u64, oracle_count_round_u64, uint64_t, 64)
+
+/* ------------------------------------------------------------------------
+ * Sample-sort partition into `parts` ranges. Splitter j (1 <= j < parts) is
+ * sorted_sample[floor(j m / parts)] (a regular choice among the m sorted
+ * sample keys); the range of key k is the number of splitters <= k, so keys
+ * equal to a splitter go to the range that splitter opens. The keys are then
+ * routed by one stable count-sort round whose digit is the range: count,
+ * exclusive prefix, output in input order. counts[r] = keys in range r.
+ * Returns 0, or -1 on bad arguments / memory.
+ * ---------------------------------------------------------------------- */
+#define DEFINE_PARTITION(NAME, KT)                                                                  \
+    int NAME(const KT* keys, const uint32_t* vals, KT* kout, uint32_t* vout, size_t n,              \
+             const KT* sorted_sample, size_t m, int parts, uint64_t* counts) {                      \
+        if (parts < 1 || parts > 256 || (parts > 1 && m < 1)) return -1;                            \
+        KT spl[256];                                                                                \
+        const int ns = parts - 1;                                                                   \
+        for (int j = 1; j < parts; ++j) spl[j - 1] = sorted_sample[(size_t)((uint64_t)j * m / (uint64_t)parts)]; \
+        uint8_t* r = (uint8_t*)malloc(n ? n : 1);                                                   \
+        if (!r) return -1;                                                                          \
+        memset(counts, 0, sizeof(uint64_t) * (size_t)parts);                                        \
+        for (size_t i = 0; i < n; ++i) {                                                            \
+            int q = 0;                                                                              \
+            if (ORACLE_MUTANT == 7) { while (q < ns && spl[q] < keys[i]) ++q; } /* planted: < */    \
+            else { while (q < ns && spl[q] <= keys[i]) ++q; }                                       \
+            r[i] = (uint8_t)q;                                                                      \
+            counts[q]++;                                                                            \
+        }                                                                                           \
+        uint64_t start[256], run = 0;                                                               \
+        for (int q = 0; q < parts; ++q) { start[q] = run; run += counts[q]; }                       \
+        for (size_t i = 0; i < n; ++i) {                                                            \
+            const uint64_t o = start[r[i]]++;                                                       \
+            kout[o] = keys[i];                                                                      \
+            if (vals) vout[o] = vals[i];                                                            \
+        }                                                                                           \
+        free(r);                                                                                    \
+        return 0;                                                                                   \
+    }
+
+DEFINE_PARTITION(oracle_partition_u32, uint32_t)
+DEFINE_PARTITION(oracle_partition_u64, uint64_t)
 
 /* Per-round digit histograms of the input: hist[d * 2^radix_bits + b] = number
  * of keys whose round-d digit equals b (the count step of Section 3's
