@@ -287,6 +287,38 @@ ISORT_API isort_status isort_mlp_loss_grad(const float* u, uint32_t m, const flo
                                            void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Sample-sort steps for a sort spread over p processes (Section 2, the sample
+ * sorts with regular sampling; the routing of keys is Section 3's count-sort
+ * round with the key's range as its digit, the key exchange of eq. Tp).
+ *
+ * isort_sample: out[j] = keys[floor(r_j * n / 2^64)] for j < m, r_j the j-th
+ *   output of SplitMix64 started at state `seed` (Steele, Lea & Flood 2014).
+ *   key_width 32 (uint32 keys) or 64 (uint64 keys); keys (n >= 1) and out (m
+ *   keys) are device memory, owned by the caller. m = 0 is a no-op.
+ *   ISORT_ERR_INVALID_ARG for another key width, n = 0 with m > 0, NULL or
+ *   host pointers.
+ * isort_partition[_u64]: the stable routing of n keys (and payloads) into
+ *   `parts` ranges. Splitter j (1 <= j < parts) is
+ *   sorted_sample[floor(j * m / parts)] (a regular choice among m sample keys
+ *   sorted ascending, e.g. the samples of all processes gathered and sorted);
+ *   the range of a key is the number of splitters <= key. keys_out/vals_out
+ *   receive range 0's keys, then range 1's, ..., each in input order;
+ *   counts[r] (uint64, `parts` entries) = keys in range r. All pointers are
+ *   device memory owned by the caller; the output must not overlap the input
+ *   (vals: both or neither). parts in 1..256 (m >= 1 when parts > 1);
+ *   n < 2^32 (larger: ISORT_ERR_UNSUPPORTED). ISORT_ERR_INVALID_ARG for other
+ *   values, NULL, host or aliased pointers. Scratch as isort_radix.
+ * ------------------------------------------------------------------------- */
+ISORT_API isort_status isort_sample(const void* keys, int key_width, size_t n, uint32_t m, uint64_t seed, void* out,
+                                    void* stream);
+ISORT_API isort_status isort_partition(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                                       uint32_t* vals_out, size_t n, const uint32_t* sorted_sample, size_t m,
+                                       int parts, uint64_t* counts, void* stream);
+ISORT_API isort_status isort_partition_u64(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
+                                           uint32_t* vals_out, size_t n, const uint64_t* sorted_sample, size_t m,
+                                           int parts, uint64_t* counts, void* stream);
+
+/* ---------------------------------------------------------------------------
  * isort_radix_noalloc: isort_radix (in place, u32 keys, optional u32 payload)
  * for callers that must not allocate memory. The paper has no counterpart; it
  * exists because some callers cannot let a library allocate device memory:

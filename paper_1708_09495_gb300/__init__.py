@@ -69,6 +69,9 @@ SIGNATURES = [
     ("isort_oet_p", _i32, [_vp, _vp, _sz, _i32, _vp, _vp]),
     ("isort_segmented", _i32, [_vp, _vp, _vp, _sz, _i32, _vp]),
     ("isort_radix_noalloc", _i32, [_vp, _vp, _sz, _i32, _i32, _vp]),
+    ("isort_sample", _i32, [_vp, _i32, _sz, ctypes.c_uint32, ctypes.c_uint64, _vp, _vp]),
+    ("isort_partition", _i32, [_vp, _vp, _vp, _vp, _sz, _vp, _sz, _i32, _vp, _vp]),
+    ("isort_partition_u64", _i32, [_vp, _vp, _vp, _vp, _sz, _vp, _sz, _i32, _vp, _vp]),
     ("isort_learned", _i32, [_vp, _vp, _sz, _i32, _i32, _i32, _vp, _vp]),
     ("isort_learned_u64", _i32, [_vp, _vp, _sz, _i32, _i32, _i32, _vp, _vp]),
     ("isort_cdf_train", _i32, [_vp, ctypes.c_uint32, _i32, _vp, _vp, _vp, _vp, _vp]),
@@ -346,6 +349,31 @@ def bucket_ids(keys, X, Y, nbuckets: int = 4096, key_bits: int = 0, stream=None)
     _check(load().isort_bucket_ids(_ptr(keys), w, keys.numel(), key_bits, _ptr(X), _ptr(Y), nbuckets, _ptr(ids),
                                    _stream(stream)), "isort_bucket_ids")
     return ids
+
+
+def sample(keys, m: int, seed: int, stream=None):
+    """m keys drawn at SplitMix64-chosen indices (a new device tensor)."""
+    import torch
+
+    out = torch.empty(m, dtype=keys.dtype, device=keys.device)
+    _check(load().isort_sample(_ptr(keys), _key_width(keys), keys.numel(), m, seed & (2**64 - 1), _ptr(out),
+                               _stream(stream)), "isort_sample")
+    return out
+
+
+def partition(keys, vals, sorted_sample, parts: int, stream=None):
+    """Stable routing of keys (and payloads) into the ranges of `parts - 1`
+    splitters chosen regularly from `sorted_sample`; returns (keys_out,
+    vals_out, counts) with counts an int64 device tensor of `parts` entries."""
+    import torch
+
+    ko = torch.empty_like(keys)
+    vo = None if vals is None else torch.empty_like(vals)
+    counts = torch.empty(parts, dtype=torch.int64, device=keys.device)
+    fn = load().isort_partition if _key_width(keys) == 32 else load().isort_partition_u64
+    _check(fn(_ptr(keys), _ptr(vals), _ptr(ko), _ptr(vo), keys.numel(), _ptr(sorted_sample), sorted_sample.numel(),
+              parts, _ptr(counts), _stream(stream)), "isort_partition")
+    return ko, vo, counts
 
 
 def autotune(enable: bool, cache_path: str | None = None):

@@ -111,4 +111,14 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 
 __device__ __forceinline__ void set_status(uint32_t* status, uint32_t bits) { atomicOr(status, bits); }
 
+// SplitMix64 (Steele, Lea & Flood 2014): output j of the generator started at
+// state s is splitmix_mix(s + (j + 1) * kSplitmixGamma). Sample indices are
+// drawn from it (index = floor(r * n / 2^64)).
+constexpr uint64_t kSplitmixGamma = 0x9E3779B97F4A7C15ull;
+__device__ __forceinline__ uint64_t splitmix_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
 }  // namespace isort

@@ -79,17 +79,10 @@ isort_status finish_buckets(uint64_t* k, uint32_t* v, const uint64_t* off, uint3
 
 constexpr uint32_t kSampleSize = 1u << 16;
 constexpr uint64_t kSampleSeed = 0x5EED5EED5EEDull;
-constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
 constexpr uint32_t kFitStride = 8;  // the fit sees every 8th point of the sorted sample
 constexpr float kLearningRate = 0.02f;
 constexpr uint32_t kOnChipCapacity = 65536;  // keys a cluster finishes on chip
 constexpr int kMaxBuckets = 32768;           // the census counts every bucket in shared memory
-
-__device__ __forceinline__ uint64_t splitmix_mix(uint64_t z) {
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
 
 // ---------------------------------------------------------------- sampling
 
@@ -97,7 +90,7 @@ template <typename K>
 __global__ void k_sample_gather(const K* __restrict__ keys, uint64_t n, uint32_t m, K* __restrict__ out) {
     const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= m) return;
-    const uint64_t r = splitmix_mix(kSampleSeed + (uint64_t)(j + 1) * kGamma);
+    const uint64_t r = splitmix_mix(kSampleSeed + (uint64_t)(j + 1) * kSplitmixGamma);
     const uint64_t idx = __umul64hi(r, n);  // floor(r * n / 2^64) < n
     out[j] = keys[idx];
 }
