@@ -632,11 +632,22 @@ def cfg_segmented(c):
 
     seg = lambda: c.ok(c.lib.isort_segmented(_vp(kw), _vp(vw), _vp(doff), nseg, 32, c.sp), "segmented")
     cmp_ = lambda: c.ok(c.lib.isort_radix_u64(_vp(cw), _vp(vw), n, cbits, 8, c.sp), "radix_u64")
-    c.isort.profile_read()
-    c.isort.profile_enable(True)
-    ms = c.time(seg, reset_s)
-    c.isort.profile_enable(False)
-    prof = c.isort.profile_read()
+    # the router's cut-offs measured on this GPU (untimed), then the timed runs
+    import tempfile
+
+    tune_path = os.path.join(tempfile.mkdtemp(prefix="isort_tune_"), "cache.txt")
+    c.isort.autotune(True, tune_path)
+    try:
+        reset_s()
+        seg()
+        router = [ln.split()[1:] for ln in open(tune_path) if ln.startswith("router")]
+        c.isort.profile_read()
+        c.isort.profile_enable(True)
+        ms = c.time(seg, reset_s)
+        c.isort.profile_enable(False)
+        prof = c.isort.profile_read()
+    finally:
+        c.isort.autotune(False)
     chk = check_pairs(keys, _host(kw, np.uint32), _host(vw, np.uint32), seg_id)
     ms_p = c.time(cmp_, reset_c)
     del kin, vin, doff, kw, vw, cin, cw
@@ -645,6 +656,9 @@ def cfg_segmented(c):
                   plain_lsd={"ms_per_call": ms_p, "call": f"isort_radix_u64 on (segment id << 32 | key), "
                                                           f"{cbits} key bits, radix 2^8"},
                   speedup_vs_plain=ms_p / ms,
+                  router_cutoffs={"payload" if r[0] == "1" else "keys_only":
+                                  {"oet_max": int(r[1]), "btn_warp_max": int(r[2]), "btn_cta_max": int(r[3])}
+                                  for r in router},
                   kernels={k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in prof.items()})
 
 

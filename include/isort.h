@@ -357,15 +357,23 @@ ISORT_API isort_status isort_radix_noalloc(uint32_t* keys, uint32_t* vals, size_
  *   wait (look-back, copy completion). A wait that runs out records
  *   ISORT_ERR_TIMEOUT and the kernel returns. Default 2,000,000 (2 s).
  * ------------------------------------------------------------------------- */
-/* Autotuning of the count-sort rounds' launch shape (the library's own choice,
- * not in the paper). enable = 1: the first radix sort of each kind (key width,
- * payload or not, digits of <= 8 bits or wider, floor(log2 n); n >= 2^20)
- * times the candidate shapes once on synthetic keys of the same size (it
- * allocates scratch and synchronises the stream; not inside a stream capture)
- * and keeps the fastest for the rest of the process; choices are read from
- * cache_path (text, one "key_bytes payload wide log2n shape" per line; NULL:
- * memory only) and appended to it. enable = 0: the built-in shapes.
- * ISORT_ERR_INVALID_ARG for other values of enable. */
+/* Autotuning (the library's own choices, not in the paper). enable = 1:
+ * - the count-sort rounds' launch shape: the first radix sort of each kind
+ *   (key width, payload or not, digits of <= 8 bits or wider, floor(log2 n);
+ *   n >= 2^20) times the candidate shapes once on synthetic keys of the same
+ *   size and keeps the fastest ("key_bytes payload wide log2n shape" lines);
+ * - the segmented router's length cut-offs between OET in a warp, BTN in a
+ *   warp, BTN over a CTA and the on-chip count-sort rounds (Section 4,
+ *   Observations 5-6: the networks win for small n): the first segmented sort
+ *   of each kind (keys only, with payloads) times every method on batches of
+ *   equal-length segments of 8..4096 keys and takes as each cut-off the
+ *   largest length at which that method was the fastest ("router payload oet
+ *   btn_warp btn_cta" lines; the built-in cut-offs are 32, 256, 4096).
+ * Timing allocates scratch and synchronises the stream; inside a stream
+ * capture the built-in (or cached) choices are used. Choices last for the
+ * process, are read from cache_path (text; NULL: memory only) and appended to
+ * it. enable = 0: the built-in choices. ISORT_ERR_INVALID_ARG for other
+ * values of enable. The sorted output never depends on these choices. */
 ISORT_API isort_status isort_autotune(int enable, const char* cache_path);
 
 ISORT_API isort_status isort_set_sync(int on);

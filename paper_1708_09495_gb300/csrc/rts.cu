@@ -409,6 +409,13 @@ template isort_status radix_device_rts<uint32_t>(const uint32_t*, const uint32_t
 template isort_status radix_device_rts<uint64_t>(const uint64_t*, const uint32_t*, uint64_t*, uint32_t*, size_t, int,
                                                  int, cudaStream_t, int);
 
+bool autotune_config(std::string* path) {
+    AutoState& as = auto_state();
+    std::lock_guard<std::mutex> lk(as.mu);
+    if (path) *path = as.path;
+    return as.enabled;
+}
+
 }  // namespace isort
 
 using namespace isort;
@@ -417,21 +424,29 @@ extern "C" {
 
 isort_status isort_autotune(int enable, const char* cache_path) {
     if (enable != 0 && enable != 1) return ISORT_ERR_INVALID_ARG;
-    AutoState& as = auto_state();
-    std::lock_guard<std::mutex> lk(as.mu);
-    as.enabled = enable == 1;
-    as.shapes.clear();
-    as.path = cache_path ? cache_path : "";
-    if (as.enabled && cache_path) {
-        if (FILE* f = std::fopen(cache_path, "r")) {
-            AutoKey k;
-            int shape = 0;
-            while (std::fscanf(f, "%d %d %d %d %d", &k.key_bytes, &k.vals, &k.wide, &k.log2n, &shape) == 5) {
-                if (shape >= 0 && shape < kNumShapes) as.shapes[k] = shape;
+    {
+        AutoState& as = auto_state();
+        std::lock_guard<std::mutex> lk(as.mu);
+        as.enabled = enable == 1;
+        as.shapes.clear();
+        as.path = cache_path ? cache_path : "";
+        if (as.enabled && cache_path) {
+            if (FILE* f = std::fopen(cache_path, "r")) {
+                // "key_bytes payload wide log2n shape" lines; lines of other
+                // kinds (the segmented router's) are read by their owner
+                char ln[256];
+                while (std::fgets(ln, sizeof(ln), f)) {
+                    AutoKey k;
+                    int shape = 0;
+                    if (std::sscanf(ln, "%d %d %d %d %d", &k.key_bytes, &k.vals, &k.wide, &k.log2n, &shape) == 5 &&
+                        shape >= 0 && shape < kNumShapes)
+                        as.shapes[k] = shape;
+                }
+                std::fclose(f);
             }
-            std::fclose(f);
         }
     }
+    router_autotune_reset();
     return ISORT_OK;
 }
 

@@ -26,13 +26,16 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
 #include "net.cuh"
 #include "runtime.h"
+#include "tune.h"
 
 namespace cg = cooperative_groups;
 
@@ -728,14 +731,6 @@ __global__ void __launch_bounds__(kSegThreads, (RB == 8 && sizeof(K) == 4) ? 2 :
 
 // ---------------------------------------------------------------- host side
 
-struct Tuned {
-    SegThresholds th{32, 256, 4096};
-};
-
-Tuned& seg_tune() {
-    static Tuned t;
-    return t;
-}
 
 template <int C>
 isort_status launch_cluster(bool vals, const ClusterArgs& a, cudaStream_t s) {
@@ -827,9 +822,8 @@ isort_status launch_split(bool vals, const SegArgsT<K>& a, cudaStream_t s) {
 
 // Enqueues classification and every class kernel on `s`.
 isort_status enqueue_segmented(uint32_t* keys, uint32_t* vals, const uint64_t* off, uint32_t nseg, int key_bits,
-                               SegCtl* ctl, uint32_t* lists, int big_ok, cudaStream_t s,
+                               SegCtl* ctl, uint32_t* lists, int big_ok, const SegThresholds& th, cudaStream_t s,
                                const uint32_t* seg_lo = nullptr, const uint8_t* seg_bits = nullptr) {
-    const SegThresholds th = seg_tune().th;
     const uint32_t range_mask = (key_bits >= 32 || seg_bits) ? 0u : ~((1u << key_bits) - 1u);
     ISORT_TRY_CUDA(cudaMemsetAsync(ctl, 0, sizeof(SegCtl), s));
     {
@@ -896,7 +890,7 @@ struct GraphCache {
 thread_local GraphCache g_graph;
 
 isort_status launch_via_graph(uint32_t* keys, uint32_t* vals, const uint64_t* off, uint32_t nseg, int key_bits,
-                              SegCtl* ctl, uint32_t* lists, int big_ok, cudaStream_t s,
+                              SegCtl* ctl, uint32_t* lists, int big_ok, const SegThresholds& th, cudaStream_t s,
                               const uint32_t* seg_lo = nullptr, const uint8_t* seg_bits = nullptr) {
     int dev = 0;
     ISORT_TRY_CUDA(cudaGetDevice(&dev));
@@ -913,7 +907,7 @@ isort_status launch_via_graph(uint32_t* keys, uint32_t* vals, const uint64_t* of
     isort_status st;
     {
         CaptureScope cs;  // launches are counted, not timed, while capturing
-        st = enqueue_segmented(keys, vals, off, nseg, key_bits, ctl, lists, big_ok, gc.cap, seg_lo, seg_bits);
+        st = enqueue_segmented(keys, vals, off, nseg, key_bits, ctl, lists, big_ok, th, gc.cap, seg_lo, seg_bits);
     }
     cudaError_t ce = cudaStreamEndCapture(gc.cap, &graph);
     if (st != ISORT_OK) {
@@ -943,6 +937,173 @@ isort_status launch_via_graph(uint32_t* keys, uint32_t* vals, const uint64_t* of
     return ISORT_OK;
 }
 
+// ---------------------------------------------------------------- router autotuning
+//
+// The length cut-offs between the classes are where one method overtakes the
+// next (Section 4, Observations 5-6: the networks win for small n, the
+// count-sort rounds for larger n; where is machine-dependent). The built-in
+// cut-offs {32, 256, 4096} are the largest lengths each network kernel takes.
+// With isort_autotune on, the first segmented sort of each kind (keys only or
+// with payloads) times each method -- OET in a warp, BTN in a warp, BTN over a
+// CTA, the one-CTA on-chip count-sort rounds -- on synthetic batches of 2^20
+// keys in segments of one length, for lengths from 8 to 4096, and takes as
+// each cut-off the largest length at which that method was the fastest; the
+// choice is appended to the cache file as "router <payload> <oet> <btn_warp>
+// <btn_cta>" and read from it later. Every method sorts every length it is
+// given stably, so the output does not depend on the cut-offs.
+constexpr SegThresholds kDefaultThresholds{32, 256, 4096};
+constexpr uint32_t kMaxOet = 32, kMaxBtnWarp = 256, kMaxBtnCta = 4096;
+
+struct RouterTune {
+    std::mutex mu;
+    bool done[2] = {false, false};
+    SegThresholds th[2] = {kDefaultThresholds, kDefaultThresholds};
+};
+
+RouterTune& router_state() {
+    static RouterTune r;
+    return r;
+}
+
+bool valid_thresholds(const SegThresholds& t) {
+    return t.oet <= kMaxOet && t.btn_warp <= kMaxBtnWarp && t.btn_cta <= kMaxBtnCta && t.oet <= t.btn_warp &&
+           t.btn_warp <= t.btn_cta;
+}
+
+__global__ void k_router_fill(uint32_t* keys, uint32_t* vals, uint32_t n, uint64_t* off, uint32_t nseg, uint32_t len) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        keys[i] = (uint32_t)(splitmix_mix(0x5E6Dull + (uint64_t)(i + 1) * kSplitmixGamma) >> 32);
+        if (vals) vals[i] = i;
+    }
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q <= nseg; q += gridDim.x * blockDim.x)
+        off[q] = (uint64_t)q * len;
+}
+
+// Times each method on segments of each length; *out gets the cut-offs.
+isort_status measure_router(bool with_vals, cudaStream_t s, SegThresholds* out) {
+    constexpr uint32_t kN = 1u << 20;
+    constexpr uint32_t kLens[] = {8, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096};
+    constexpr uint32_t kMaxSeg = kN / 8;
+    const size_t kb = (size_t)kN * 4, ob = align_up((size_t)(kMaxSeg + 1) * 8, 256);
+    const size_t ctl_bytes = align_up(sizeof(SegCtl), 256), list_bytes = align_up((size_t)kNumCls * kMaxSeg * 4, 256);
+    const size_t total = 4 * kb + ob + ctl_bytes + list_bytes;
+    unsigned char* ws = nullptr;
+    ISORT_TRY(scratch_alloc((void**)&ws, total, s));
+    uint32_t* k0 = reinterpret_cast<uint32_t*>(ws);
+    uint32_t* v0 = reinterpret_cast<uint32_t*>(ws + kb);
+    uint32_t* k = reinterpret_cast<uint32_t*>(ws + 2 * kb);
+    uint32_t* v = reinterpret_cast<uint32_t*>(ws + 3 * kb);
+    uint64_t* off = reinterpret_cast<uint64_t*>(ws + 4 * kb);
+    SegCtl* ctl = reinterpret_cast<SegCtl*>(ws + 4 * kb + ob);
+    uint32_t* lists = reinterpret_cast<uint32_t*>(ws + 4 * kb + ob + ctl_bytes);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    // method m: the thresholds that send every segment of up to its limit to it
+    const SegThresholds route[4] = {{kMaxOet, kMaxOet, kMaxOet}, {0, kMaxBtnWarp, kMaxBtnWarp}, {0, 0, kMaxBtnCta},
+                                    {0, 0, 0}};
+    const uint32_t limit[4] = {kMaxOet, kMaxBtnWarp, kMaxBtnCta, (uint32_t)kSegChunk};
+    uint32_t best_len[3] = {0, 0, 0};  // largest length where OET / BTN warp / BTN CTA was the fastest
+    isort_status st = ISORT_OK;
+    for (uint32_t len : kLens) {
+        const uint32_t nseg = kN / len;
+        k_router_fill<<<4 * sm_count(), 256, 0, s>>>(k0, with_vals ? v0 : nullptr, kN, off, nseg, len);
+        float best = 1e30f;
+        int win = -1;
+        for (int m = 0; m < 4 && st == ISORT_OK; ++m) {
+            if (len > limit[m]) continue;
+            float t_best = 1e30f;
+            for (int rep = 0; rep < 3 && st == ISORT_OK; ++rep) {
+                cudaMemcpyAsync(k, k0, kb, cudaMemcpyDeviceToDevice, s);
+                if (with_vals) cudaMemcpyAsync(v, v0, kb, cudaMemcpyDeviceToDevice, s);
+                cudaEventRecord(e0, s);
+                st = enqueue_segmented(k, with_vals ? v : nullptr, off, nseg, 32, ctl, lists, 0, route[m], s);
+                cudaEventRecord(e1, s);
+                if (st == ISORT_OK && cudaEventSynchronize(e1) == cudaSuccess) {
+                    float t = 0.f;
+                    cudaEventElapsedTime(&t, e0, e1);
+                    t_best = std::min(t_best, t);
+                } else if (st == ISORT_OK) {
+                    st = ISORT_ERR_CUDA;
+                }
+            }
+            if (t_best < best) {
+                best = t_best;
+                win = m;
+            }
+        }
+        if (st != ISORT_OK) break;
+        if (win >= 0 && win < 3) best_len[win] = len;
+    }
+    uint32_t dev_status = 0;
+    if (st == ISORT_OK) {
+        if (cudaMemcpyAsync(&dev_status, &ctl->status, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            st = ISORT_ERR_CUDA;
+        else if (dev_status)
+            st = map_bits(dev_status);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    scratch_free(ws, s);
+    cudaStreamSynchronize(s);
+    if (st != ISORT_OK) return st;
+    SegThresholds t;
+    t.oet = best_len[0];
+    t.btn_warp = std::max(t.oet, best_len[1]);
+    t.btn_cta = std::max(t.btn_warp, best_len[2]);
+    *out = t;
+    return ISORT_OK;
+}
+
+// The cut-offs a segmented sort uses (the built-in ones unless autotuning is on).
+isort_status router_thresholds(bool with_vals, cudaStream_t s, SegThresholds* th) {
+    std::string path;
+    *th = kDefaultThresholds;
+    if (!autotune_config(&path)) return ISORT_OK;
+    RouterTune& rt = router_state();
+    std::lock_guard<std::mutex> lk(rt.mu);
+    const int kind = with_vals ? 1 : 0;
+    if (rt.done[kind]) {
+        *th = rt.th[kind];
+        return ISORT_OK;
+    }
+    if (!path.empty()) {
+        if (FILE* f = std::fopen(path.c_str(), "r")) {
+            char ln[256];
+            while (std::fgets(ln, sizeof(ln), f)) {
+                int pv = -1;
+                SegThresholds t{};
+                if (std::sscanf(ln, "router %d %u %u %u", &pv, &t.oet, &t.btn_warp, &t.btn_cta) == 4 && pv == kind &&
+                    valid_thresholds(t)) {
+                    rt.th[kind] = t;
+                    rt.done[kind] = true;
+                }
+            }
+            std::fclose(f);
+        }
+        if (rt.done[kind]) {
+            *th = rt.th[kind];
+            return ISORT_OK;
+        }
+    }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cap);
+    if (cap != cudaStreamCaptureStatusNone) return ISORT_OK;  // no timing inside a capture: built-in cut-offs
+    SegThresholds t;
+    ISORT_TRY(measure_router(with_vals, s, &t));
+    rt.th[kind] = t;
+    rt.done[kind] = true;
+    *th = t;
+    if (!path.empty()) {
+        if (FILE* f = std::fopen(path.c_str(), "a")) {
+            std::fprintf(f, "router %d %u %u %u\n", kind, t.oet, t.btn_warp, t.btn_cta);
+            std::fclose(f);
+        }
+    }
+    return ISORT_OK;
+}
+
 isort_status segmented_entry(uint32_t* keys, uint32_t* vals, const uint64_t* off, size_t nseg, int key_bits,
                              void* stream, const uint32_t* seg_lo = nullptr, const uint8_t* seg_bits = nullptr) {
     if (key_bits == 0) key_bits = 32;
@@ -953,6 +1114,8 @@ isort_status segmented_entry(uint32_t* keys, uint32_t* vals, const uint64_t* off
     if (is_host_pointer(keys) || is_host_pointer(off) || (vals && is_host_pointer(vals))) return ISORT_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const uint32_t ns = (uint32_t)nseg;
+    SegThresholds th;
+    ISORT_TRY(router_thresholds(vals != nullptr, s, &th));
     const size_t ctl_bytes = align_up(sizeof(SegCtl), 256);
     const size_t list_bytes = align_up((size_t)kNumCls * ns * 4, 256);
     unsigned char* ws = nullptr;
@@ -966,9 +1129,9 @@ isort_status segmented_entry(uint32_t* keys, uint32_t* vals, const uint64_t* off
     const int big_ok = sync_mode() && cap != cudaStreamCaptureStatusActive;
     if (cap == cudaStreamCaptureStatusActive || trace_on()) {
         // the caller is building its own graph (or launches are traced): enqueue directly
-        st = enqueue_segmented(keys, vals, off, ns, key_bits, ctl, lists, big_ok, s, seg_lo, seg_bits);
+        st = enqueue_segmented(keys, vals, off, ns, key_bits, ctl, lists, big_ok, th, s, seg_lo, seg_bits);
     } else {
-        st = launch_via_graph(keys, vals, off, ns, key_bits, ctl, lists, big_ok, s, seg_lo, seg_bits);
+        st = launch_via_graph(keys, vals, off, ns, key_bits, ctl, lists, big_ok, th, s, seg_lo, seg_bits);
     }
     if (st != ISORT_OK) {
         scratch_free(ws, s);
@@ -1010,6 +1173,13 @@ isort_status segmented_entry(uint32_t* keys, uint32_t* vals, const uint64_t* off
 }
 
 }  // namespace
+
+void router_autotune_reset() {
+    RouterTune& rt = router_state();
+    std::lock_guard<std::mutex> lk(rt.mu);
+    rt.done[0] = rt.done[1] = false;
+    rt.th[0] = rt.th[1] = kDefaultThresholds;
+}
 
 // The finishing step of the learned-bucket sort: every bucket is a segment
 // whose keys lie in [seg_lo[s], seg_lo[s] + 2^seg_bits[s]).

@@ -2,6 +2,8 @@
 // the single-pass rounds (radix.cu) and the chunked rounds (rts.cu).
 #pragma once
 
+#include <string>
+
 namespace isort {
 
 // Defaults are the measured best on GB300; the environment variable
@@ -20,5 +22,11 @@ struct Tune {
 };
 
 const Tune& tune();
+
+// The autotuning switch of isort_autotune: true when on; *path is the cache
+// file ("" for memory only).
+bool autotune_config(std::string* path);
+// Forgets the segmented router's tuned thresholds (isort_autotune calls it).
+void router_autotune_reset();
 
 }  // namespace isort

@@ -2,6 +2,8 @@
 every routing class (OET, warp BTN, CTA BTN, clusters of 1/2/4/8 CTAs, and the
 long-segment path), empty and one-key segments, key ranges, payloads, graph
 reuse, error paths, and the full 200,000-length workload capped at 2^28 keys."""
+import os
+
 import numpy as np
 import pytest
 
@@ -156,3 +158,43 @@ def test_full_segmented_workload(cuda_lib):
     gk, gv = run(cuda_lib, keys, vals, off)
     rk, rv = oracle.segmented(keys, vals, off, 32, 8)
     assert np.array_equal(gk, rk) and np.array_equal(gv, rv)
+
+
+def _router_lines(path):
+    out = {}
+    if os.path.exists(path):
+        for ln in open(path):
+            p = ln.split()
+            if p and p[0] == "router":
+                out.setdefault(int(p[1]), []).append(tuple(int(x) for x in p[2:5]))
+    return out
+
+
+def test_router_autotune_cache_and_parity(cuda_lib, tmp_path):
+    """The router's cut-offs measured on this GPU: written to the cache once per
+    kind, read back after a reset instead of measured again, within the
+    kernels' limits; and the sort bit-exact against the oracle with the tuned
+    cut-offs and with planted ones."""
+    lengths = [2, 7, 20, 32, 33, 60, 128, 255, 300, 700, 1500, 3000, 4096, 5000, 8192, 9000, 20000] * 3
+    keys, vals, off = make(lengths, 97)
+    path = str(tmp_path / "tune.txt")
+    try:
+        cuda_lib.autotune(True, path)
+        check(cuda_lib, keys, vals, off)  # payload: measures and appends "router 1 ..."
+        check(cuda_lib, keys, None, off)  # keys only: "router 0 ..."
+        lines = _router_lines(path)
+        assert sorted(lines) == [0, 1] and all(len(v) == 1 for v in lines.values())
+        for oet, bw, bc in (lines[0][0], lines[1][0]):
+            assert 0 <= oet <= 32 and oet <= bw <= 256 and bw <= bc <= 4096
+        cuda_lib.autotune(True, path)  # reset: the cut-offs now come from the file
+        check(cuda_lib, keys, vals, off)
+        assert _router_lines(path) == lines
+        planted = str(tmp_path / "planted.txt")
+        with open(planted, "w") as f:  # every segment to the on-chip count-sort rounds / to the networks
+            f.write("router 1 0 0 0\nrouter 0 32 256 4096\n")
+        cuda_lib.autotune(True, planted)
+        check(cuda_lib, keys, vals, off)
+        check(cuda_lib, keys, None, off)
+        assert _router_lines(planted) == {1: [(0, 0, 0)], 0: [(32, 256, 4096)]}
+    finally:
+        cuda_lib.autotune(False)
