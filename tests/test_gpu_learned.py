@@ -297,11 +297,20 @@ def test_regular_sampling_matches_oracle(cuda_lib, kind):
     assert st["train_steps"] == 0 and st["train_loss"] == st["train_loss_initial"]
 
 
-@pytest.mark.parametrize("kind", ["zipf", "lognormal", "gmm"])
-def test_trained_model_vs_regular_sampling(cuda_lib, kind):
-    """What training adds to the method without it: the trained piecewise-
-    linear model starts from the regular-sampling table and keeps the best
-    parameters, so its sample loss is never higher; both sorts are exact."""
+def _equal_width_imbalance(keys, nbuckets):
+    """max / mean bucket size of the plain MSD split (top bits of the key: the
+    bucketing without any CDF model)."""
+    counts = np.bincount(keys >> np.uint32(32 - int(np.log2(nbuckets))), minlength=nbuckets)
+    return counts.max() / (keys.size / nbuckets)
+
+
+@pytest.mark.parametrize("kind", ["lognormal", "gmm"])
+def test_trained_model_vs_the_method_without_it(cuda_lib, kind):
+    """What training buys, measured: the fit lowers the sample loss of its
+    regular-sampling start (it can fail to: the assertion is strict); the
+    model's buckets are far better balanced than the plain MSD split by the
+    top bits of the key; and against regular sampling itself (Section 2) the
+    trained model is no worse balanced. All three sorts are exact."""
     keys = _keys(kind)
     ek, _ = oracle.lsd(keys, None, 0, 8)
     res = {}
@@ -309,5 +318,21 @@ def test_trained_model_vs_regular_sampling(cuda_lib, kind):
         dk = to_dev(keys)
         res[model] = cuda_lib.learned(dk, None, model=model)
         assert np.array_equal(to_np(dk, np.uint32), ek)
-    print(kind, {m: (r["train_loss"], r["imbalance_max_over_mean"]) for m, r in res.items()})
-    assert res[0]["train_loss"] <= res[2]["train_loss"] * (1 + 1e-5)
+    B = res[0]["nbuckets"]
+    plain = _equal_width_imbalance(keys, B)
+    print(kind, "equal-width", plain, {m: (r["train_loss_initial"], r["train_loss"], r["imbalance_max_over_mean"],
+                                           r["overflow_fraction"]) for m, r in res.items()})
+    # each fit makes progress from its start (the piecewise-linear model starts
+    # from the regular-sampling table itself)
+    assert res[0]["train_loss"] < 0.99 * res[0]["train_loss_initial"]
+    assert res[0]["train_loss_initial"] == pytest.approx(res[2]["train_loss"], rel=1e-6)
+    assert res[1]["train_loss"] < 0.5 * res[1]["train_loss_initial"]
+    # the CDF model (trained or regular) against no model at all
+    for m in (0, 1, 2):
+        assert res[m]["imbalance_max_over_mean"] < plain
+    # trained against regular sampling: not worse balanced (measured: the
+    # piecewise-linear fit leaves the balance where its quantile start has it;
+    # the MLP is 2-11 % better balanced)
+    for m in (0, 1):
+        assert res[m]["imbalance_max_over_mean"] <= res[2]["imbalance_max_over_mean"] * 1.05
+        assert res[m]["overflow_fraction"] <= res[2]["overflow_fraction"] + 0.01
