@@ -946,12 +946,18 @@ isort_status learned_entry(K* keys, uint32_t* vals, size_t n, int key_bits, int 
     if (key_bits == 0) key_bits = kw;
     if (key_bits < 1 || key_bits > kw) return ISORT_ERR_INVALID_ARG;
     if (nbuckets == 0) {
-        // 4096 buckets, doubled (up to the table limit) while the mean bucket
-        // would exceed a quarter of the on-chip capacity (u32) or one CTA's
-        // 8,192 keys (u64, whose clusters cost more per key)
-        const uint64_t mean_max = sizeof(K) == 4 ? kOnChipCapacity / 4 : kOnChipCapacity / 8;
-        nbuckets = 4096;
-        while (nbuckets < kMaxBuckets && (uint64_t)nbuckets * mean_max < n) nbuckets <<= 1;
+        if constexpr (sizeof(K) == 4) {
+            // 4096 buckets, doubled (up to the table limit) while the mean
+            // bucket would exceed a quarter of the on-chip capacity
+            nbuckets = 4096;
+            while (nbuckets < kMaxBuckets && (uint64_t)nbuckets * (kOnChipCapacity / 4) < n) nbuckets <<= 1;
+        } else {
+            // u64: a multiple of 4096 with a mean bucket of at most 6,656 keys,
+            // so that buckets (about +-1.5 % apart at these sizes) stay within
+            // one CTA's 8,192 keys, the fine finish's class
+            const uint64_t want = (n + 4096ull * 6656 - 1) / (4096ull * 6656);
+            nbuckets = (int)std::min<uint64_t>(std::max<uint64_t>(want, 1), kMaxBuckets / 4096) * 4096;
+        }
     }
     if (nbuckets < 2 || nbuckets > kMaxBuckets) return ISORT_ERR_INVALID_ARG;
     if (model < 0 || model > 2) return ISORT_ERR_INVALID_ARG;

@@ -58,6 +58,7 @@ static Tune load_tune() {
         else if (!strcmp(key, "split")) t.split = val;
         else if (!strcmp(key, "copy_pieces")) t.copy_pieces = val;
         else if (!strcmp(key, "small")) t.small = val;
+        else if (!strcmp(key, "fine")) t.fine = val;
         p += used;
         if (*p == ',') ++p;
     }

@@ -66,6 +66,7 @@ enum : int {
     kClsC4,
     kClsC8,
     kClsBig,
+    kClsRedo,  // segments the fine finish hands back to the split kernel
     kNumCls
 };
 
@@ -159,6 +160,7 @@ struct SegArgsT {
     uint32_t single_n = 0;    // > 0: one segment [0, single_n) (off, list and counts unused)
     K* keys_out = nullptr;    // single segment: the result goes here (keys / vals only read)
     uint32_t* vals_out = nullptr;
+    uint32_t* redo_list = nullptr;  // fine finish: where segments it leaves unsorted are listed
 };
 using ClusterArgs = SegArgsT<uint32_t>;
 
@@ -729,6 +731,262 @@ __global__ void __launch_bounds__(kSegThreads, (RB == 8 && sizeof(K) == 4) ? 2 :
     cluster.sync();  // no CTA leaves while others may still read its shared memory
 }
 
+// ---------------------------------------------------------------- fine finish
+//
+// One CTA per segment of at most 8,192 keys (u32 or u64, optional payload):
+// the segment is sorted stably on chip by the top 16 bits of (key - m) over
+// the bits its observed range spans (m its smallest key, M its largest): two
+// stable count-sort passes of 8 bits, low digit first (Section 3's round, on
+// chip). Keys sharing those 16 bits form runs of about n / 65,536 keys; each
+// run is then sorted on its remaining low bits: runs of up to kFineThreadRun
+// keys by one thread (stable insertion), runs of up to 512 keys by a warp (the
+// packed bitonic network, items (low bits << index bits | index)). A segment
+// holding a longer run is left unchanged and listed for the split kernel; a
+// segment whose keys are all equal is already in order.
+constexpr int kFineThreadRun = 16;
+constexpr int kFineMaxRuns = 512;  // runs handed to warps per segment
+constexpr int kFineBins = 256;
+
+template <typename K, bool VALS>
+constexpr size_t fine_smem_bytes() {
+    return (size_t)kSegChunk * (sizeof(K) + (VALS ? 4 : 0))  // staging
+           + (size_t)kSegWarps * kFineBins * 2                // per-warp digit counts
+           + (size_t)kSegWarps * kFineBins * 4                // per-warp peer masks
+           + (size_t)kFineBins * 4 + 128 * 4                  // digit starts, reductions and flags
+           + (size_t)kFineMaxRuns * 8;                        // long runs: start, length
+}
+
+template <typename K>
+__device__ __forceinline__ K warp_min(K x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const K y = __shfl_xor_sync(kFullMask, x, o);
+        x = y < x ? y : x;
+    }
+    return x;
+}
+
+template <typename K>
+__device__ __forceinline__ K warp_max(K x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const K y = __shfl_xor_sync(kFullMask, x, o);
+        x = y > x ? y : x;
+    }
+    return x;
+}
+
+template <typename K, bool VALS>
+__global__ void __launch_bounds__(kSegThreads, 1) k_seg_fine(SegArgsT<K> a) {
+    constexpr int KW = (int)sizeof(K) * 8;
+    constexpr int BINS = kFineBins;
+    extern __shared__ __align__(16) unsigned char smem[];
+    K* s_keys = reinterpret_cast<K*>(smem);
+    uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + kSegChunk);
+    uint16_t* s_cnt = reinterpret_cast<uint16_t*>(smem + (size_t)kSegChunk * (sizeof(K) + (VALS ? 4 : 0)));
+    uint32_t* s_match = reinterpret_cast<uint32_t*>(s_cnt + kSegWarps * BINS);
+    uint32_t* s_start = s_match + kSegWarps * BINS;  // [BINS]
+    uint32_t* s_misc = s_start + BINS;              // [128]: warp minima / maxima (as K), scan sums, flags
+    K* s_wmin = reinterpret_cast<K*>(s_misc);       // [16]
+    K* s_wmax = s_wmin + kSegWarps;                 // [16]
+    uint32_t* s_wsum = s_misc + 2 * kSegWarps * (int)(sizeof(K) / 4);  // [16], after the minima and maxima
+    uint32_t* s_flag = s_wsum + kSegWarps;          // [0] runs handed to warps, [1] redo
+    uint2* s_runs = reinterpret_cast<uint2*>(s_misc + 128);
+    if ((size_t)(reinterpret_cast<unsigned char*>(s_runs + kFineMaxRuns) - smem) > dynamic_smem_size()) {
+        if (threadIdx.x == 0) set_status(&a.ctl->status, kStatBounds);
+        return;
+    }
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt = lanemask_lt();
+    const uint32_t cnt = a.ctl->counts[a.cls];
+    for (int i = tid; i < kSegWarps * BINS; i += kSegThreads) {
+        s_cnt[i] = 0;
+        s_match[i] = 0;
+    }
+    __syncthreads();
+    for (uint32_t q = blockIdx.x; q < cnt; q += gridDim.x) {
+        const uint32_t s = a.list[q];
+        const uint64_t seg0 = a.off[s];
+        const uint32_t L = (uint32_t)(a.off[s + 1] - seg0);
+        K* gk = a.keys + seg0;
+        uint32_t* gv = VALS ? a.vals + seg0 : nullptr;
+        const K base = a.seg_lo ? a.seg_lo[s] : (K)0;
+        const int check_bits = a.seg_bits ? KW : a.key_bits;
+        if (L > (uint32_t)kSegChunk) {  // not this class's segment (never expected)
+            if (tid == 0) set_status(&a.ctl->status, kStatBounds);
+            continue;
+        }
+        // load in input order: item i of lane l of warp w is key w * 512 + 32 i + l
+        K k[kSegItems];
+        uint32_t v[kSegItems];
+        K mn = ~(K)0, mx = 0, orv = 0;
+#pragma unroll
+        for (int i = 0; i < kSegItems; ++i) {
+            const uint32_t j = (uint32_t)(warp * kSegItems * 32 + i * 32 + lane);
+            const bool valid = j < L;
+            k[i] = valid ? gk[j] : (K)0;
+            if constexpr (VALS) v[i] = valid ? gv[j] : 0u;
+            if (valid) {
+                orv |= k[i];
+                const K x = k[i] - base;
+                mn = x < mn ? x : mn;
+                mx = x > mx ? x : mx;
+            }
+        }
+        mn = warp_min(mn);
+        mx = warp_max(mx);
+        if (lane == 0) {
+            s_wmin[warp] = mn;
+            s_wmax[warp] = mx;
+        }
+        const int bad = __syncthreads_or(check_bits < KW && (orv >> check_bits) != 0);
+        if (bad) {  // a key beyond the declared range: the segment is left unchanged
+            if (tid == 0) set_status(&a.ctl->status, kStatKeyRange);
+            __syncthreads();
+            continue;
+        }
+        mn = s_wmin[0];
+        mx = s_wmax[0];
+        for (int w = 1; w < kSegWarps; ++w) {
+            const K a0 = s_wmin[w], a1 = s_wmax[w];
+            mn = a0 < mn ? a0 : mn;
+            mx = a1 > mx ? a1 : mx;
+        }
+        if (tid == 0) {
+            s_flag[0] = 0;
+            s_flag[1] = 0;
+        }
+        __syncthreads();
+        if (mx == mn) continue;  // every key equal: already in order (uniform)
+        const K span = mx - mn;
+        const int sbits = KW - (sizeof(K) == 8 ? __clzll((long long)span) : __clz((int)span));
+        const int t = sbits > 16 ? sbits - 16 : 0;  // (x - mn) >> t < 2^16
+        const int npass = sbits - t > 8 ? 2 : 1;
+        for (int pass = 0; pass < npass; ++pass) {
+            if (pass == 1) {  // the first pass's order, from the staging buffer
+#pragma unroll
+                for (int i = 0; i < kSegItems; ++i) {
+                    const uint32_t j = (uint32_t)(warp * kSegItems * 32 + i * 32 + lane);
+                    k[i] = j < L ? s_keys[j] : (K)0;
+                    if constexpr (VALS) v[i] = j < L ? s_vals[j] : 0u;
+                }
+            }
+            const int dsh = t + 8 * pass;
+            uint32_t rank[kSegItems];
+#pragma unroll
+            for (int i = 0; i < kSegItems; ++i) {
+                const uint32_t j = (uint32_t)(warp * kSegItems * 32 + i * 32 + lane);
+                const bool valid = j < L;
+                const uint32_t dg = (uint32_t)((k[i] - base - mn) >> dsh) & (uint32_t)(BINS - 1);
+                uint32_t* mw = &s_match[warp * BINS + dg];
+                if (valid) atomicOr(mw, 1u << lane);
+                __syncwarp();
+                const uint32_t peers = valid ? *mw : 0u;
+                const uint32_t below = (uint32_t)__popc(peers & lt);
+                const uint32_t c = valid ? (uint32_t)s_cnt[warp * BINS + dg] : 0u;
+                rank[i] = c + below;
+                __syncwarp();
+                if (valid && below + 1 == (uint32_t)__popc(peers)) {
+                    s_cnt[warp * BINS + dg] = (uint16_t)(c + below + 1);
+                    *mw = 0u;
+                }
+                __syncwarp();
+            }
+            __syncthreads();
+            if (tid < BINS) {  // per-warp counts -> per-warp exclusive prefixes; digit totals
+                uint32_t sum = 0;
+#pragma unroll 4
+                for (int w = 0; w < kSegWarps; ++w) {
+                    const uint32_t c = s_cnt[w * BINS + tid];
+                    s_cnt[w * BINS + tid] = (uint16_t)sum;
+                    sum += c;
+                }
+                s_start[tid] = sum;
+            }
+            scan_bins<BINS>(s_start, s_wsum);  // synchronises
+#pragma unroll
+            for (int i = 0; i < kSegItems; ++i) {
+                const uint32_t j = (uint32_t)(warp * kSegItems * 32 + i * 32 + lane);
+                if (j < L) {
+                    const uint32_t dg = (uint32_t)((k[i] - base - mn) >> dsh) & (uint32_t)(BINS - 1);
+                    const uint32_t p = s_start[dg] + s_cnt[warp * BINS + dg] + rank[i];
+                    if (p < (uint32_t)kSegChunk) {
+                        s_keys[p] = k[i];
+                        if constexpr (VALS) s_vals[p] = v[i];
+                    }
+                }
+            }
+            __syncthreads();
+            for (int i = tid; i < kSegWarps * BINS; i += kSegThreads) s_cnt[i] = 0;
+            __syncthreads();  // cleared before the next pass (or segment) ranks
+        }
+        if (t > 0) {
+            // runs of keys sharing the top 16 bits, sorted on the low t bits
+            const K lowmask = ((K)1 << t) - (K)1;
+            for (uint32_t j = (uint32_t)tid; j < L; j += kSegThreads) {
+                const K xj = s_keys[j] - base - mn;
+                const K dj = xj >> t;
+                if (j > 0 && ((s_keys[j - 1] - base - mn) >> t) == dj) continue;  // not a run start
+                uint32_t e = j + 1;
+                while (e < L && e - j <= (uint32_t)kSplitWarpMax && ((s_keys[e] - base - mn) >> t) == dj) ++e;
+                const uint32_t r = e - j;
+                if (r < 2) continue;
+                if (r <= (uint32_t)kFineThreadRun) {  // stable insertion on the low bits
+                    for (uint32_t u = j + 1; u < e; ++u) {
+                        const K ku = s_keys[u];
+                        uint32_t vu = 0;
+                        if constexpr (VALS) vu = s_vals[u];
+                        const K lu = (ku - base - mn) & lowmask;
+                        uint32_t w = u;
+                        while (w > j && ((s_keys[w - 1] - base - mn) & lowmask) > lu) {
+                            s_keys[w] = s_keys[w - 1];
+                            if constexpr (VALS) s_vals[w] = s_vals[w - 1];
+                            --w;
+                        }
+                        s_keys[w] = ku;
+                        if constexpr (VALS) s_vals[w] = vu;
+                    }
+                } else if (r > (uint32_t)kSplitWarpMax || !group_packs<VALS, K>(r, t)) {
+                    s_flag[1] = 1;  // beyond a warp's network: the split kernel takes the segment
+                } else {
+                    const uint32_t slot = atomicAdd(&s_flag[0], 1u);
+                    if (slot < (uint32_t)kFineMaxRuns) s_runs[slot] = make_uint2(j, r);
+                    else s_flag[1] = 1;
+                }
+            }
+            __syncthreads();
+            if (s_flag[1]) {  // uniform: hand the whole segment to the split kernel
+                if (tid == 0) {
+                    const uint32_t slot = atomicAdd(&a.ctl->counts[kClsRedo], 1u);
+                    a.redo_list[slot] = s;
+                }
+                __syncthreads();
+                continue;
+            }
+            const uint32_t nruns = s_flag[0];
+            for (uint32_t ri = (uint32_t)warp; ri < nruns; ri += kSegWarps) {
+                const uint2 run = s_runs[ri];
+                K* rk = s_keys + run.x;
+                uint32_t* rv = VALS ? s_vals + run.x : nullptr;
+                const K gkb = base + mn + (((rk[0] - base - mn) >> t) << t);
+                const int ib = VALS ? 32 - __clz(run.y) : 0;
+                if (run.y <= 32) btn_warp_packed<1, VALS, K>(rk, rv, rk, rv, run.y, gkb, ib);
+                else if (run.y <= 64) btn_warp_packed<2, VALS, K>(rk, rv, rk, rv, run.y, gkb, ib);
+                else if (run.y <= 128) btn_warp_packed<4, VALS, K>(rk, rv, rk, rv, run.y, gkb, ib);
+                else if (run.y <= 256) btn_warp_packed<8, VALS, K>(rk, rv, rk, rv, run.y, gkb, ib);
+                else btn_warp_packed<16, VALS, K>(rk, rv, rk, rv, run.y, gkb, ib);
+                __syncwarp();
+            }
+            __syncthreads();
+        }
+        for (uint32_t j = (uint32_t)tid; j < L; j += kSegThreads) {
+            gk[j] = s_keys[j];
+            if constexpr (VALS) gv[j] = s_vals[j];
+        }
+        __syncthreads();  // the staging buffer is refilled by the next segment
+    }
+}
+
 // ---------------------------------------------------------------- host side
 
 
@@ -820,6 +1078,19 @@ isort_status launch_split(bool vals, const SegArgsT<K>& a, cudaStream_t s) {
     return ISORT_OK;
 }
 
+template <typename K>
+isort_status launch_fine(bool vals, const SegArgsT<K>& a, cudaStream_t s) {
+    const size_t smem = vals ? fine_smem_bytes<K, true>() : fine_smem_bytes<K, false>();
+    auto kern = vals ? k_seg_fine<K, true> : k_seg_fine<K, false>;
+    ISORT_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    ISORT_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSegThreads, smem));
+    if (per_sm < 1) return ISORT_ERR_UNSUPPORTED;
+    LaunchScope ls("seg_fine", s);
+    kern<<<per_sm * sm_count(), kSegThreads, smem, s>>>(a);
+    return from_cuda(cudaGetLastError());
+}
+
 // Enqueues classification and every class kernel on `s`.
 isort_status enqueue_segmented(uint32_t* keys, uint32_t* vals, const uint64_t* off, uint32_t nseg, int key_bits,
                                SegCtl* ctl, uint32_t* lists, int big_ok, const SegThresholds& th, cudaStream_t s,
@@ -846,10 +1117,21 @@ isort_status enqueue_segmented(uint32_t* keys, uint32_t* vals, const uint64_t* o
     for (int c : order) {
         a.cls = c;
         a.list = lists + (size_t)c * nseg;
-        isort_status st = c == kClsC8   ? launch_split<8>(v, a, s)
-                          : c == kClsC4 ? launch_split<4>(v, a, s)
-                          : c == kClsC2 ? launch_split<2>(v, a, s)
-                                        : launch_cluster<1>(v, a, s);
+        isort_status st;
+        if (c == kClsC1 && tune().fine) {  // the fine finish; what it hands back takes the on-chip rounds
+            a.redo_list = lists + (size_t)kClsRedo * nseg;
+            st = launch_fine<uint32_t>(v, a, s);
+            if (st == ISORT_OK) {
+                a.cls = kClsRedo;
+                a.list = a.redo_list;
+                st = launch_cluster<1>(v, a, s);
+            }
+        } else {
+            st = c == kClsC8   ? launch_split<8>(v, a, s)
+                 : c == kClsC4 ? launch_split<4>(v, a, s)
+                 : c == kClsC2 ? launch_split<2>(v, a, s)
+                               : launch_cluster<1>(v, a, s);
+        }
         if (st != ISORT_OK) return st;
     }
     {
@@ -1258,10 +1540,20 @@ isort_status segmented_finish_u64(uint64_t* keys, uint32_t* vals, const uint64_t
     for (int c : order) {
         a.cls = c;
         a.list = lists + (size_t)c * nseg;
-        st = c == kClsC8   ? launch_split<8, uint64_t>(v, a, s)
-             : c == kClsC4 ? launch_split<4, uint64_t>(v, a, s)
-             : c == kClsC2 ? launch_split<2, uint64_t>(v, a, s)
-                           : launch_split<1, uint64_t>(v, a, s);
+        if (c == kClsC1 && tune().fine) {  // the fine finish; what it hands back takes the split kernel
+            a.redo_list = lists + (size_t)kClsRedo * nseg;
+            st = launch_fine<uint64_t>(v, a, s);
+            if (st == ISORT_OK) {
+                a.cls = kClsRedo;
+                a.list = a.redo_list;
+                st = launch_split<1, uint64_t>(v, a, s);
+            }
+        } else {
+            st = c == kClsC8   ? launch_split<8, uint64_t>(v, a, s)
+                 : c == kClsC4 ? launch_split<4, uint64_t>(v, a, s)
+                 : c == kClsC2 ? launch_split<2, uint64_t>(v, a, s)
+                               : launch_split<1, uint64_t>(v, a, s);
+        }
         if (st != ISORT_OK) break;
     }
     if (st == ISORT_OK) st = finish_status(&ctl->status, s);  // a longer segment sets "unsupported"

@@ -18,6 +18,7 @@ struct Tune {
     int sweep_large = 2;  // chunked-round launch shape, wider digits
     int small = 1;        // u32 sorts of <= 65,536 keys in place at radix 2^8: one on-chip cluster launch
     int split = 8;
+    int fine = 1;         // segments of <= 8,192 keys: 1 the fine finish (two 8-bit passes + runs), 0 the older kernels
     int copy_pieces = 4;  // host-buffer staging copies: at most this many pieces on auxiliary streams        // chunked rounds: a digit wider than this runs as two stable passes (8..16)
 };
 

@@ -198,3 +198,41 @@ def test_router_autotune_cache_and_parity(cuda_lib, tmp_path):
         assert _router_lines(planted) == {1: [(0, 0, 0)], 0: [(32, 256, 4096)]}
     finally:
         cuda_lib.autotune(False)
+
+
+def _fine_segments(seed):
+    """Segments of 4,097..8,192 keys (the one-CTA class) that drive every path
+    of the fine finish: uniform keys (short runs), clusters of 10 / 20 / 300
+    distinct keys under a far outlier (insertion, warp network), clusters of
+    600 and 7,000 (runs too long: handed to the other kernel), all keys equal,
+    ranges of 200 and 4,096 values (one or two passes, no runs)."""
+    r = np.random.default_rng(seed)
+    segs = []
+
+    def uni(n, hi=2**32):
+        return r.integers(0, hi, n, dtype=np.uint64).astype(np.uint32)
+
+    segs.append(uni(8192))
+    segs.append(uni(4097))
+    for c in (10, 20, 300, 600):
+        x = uni(5000 - c - 1)
+        x = np.concatenate([x, (100 + r.permutation(c)).astype(np.uint32), np.array([2**32 - 1], np.uint32)])
+        segs.append(r.permutation(x).astype(np.uint32))
+    x = np.concatenate([(1000 + r.permutation(7000)).astype(np.uint32), uni(100), np.array([2**32 - 1], np.uint32)])
+    segs.append(r.permutation(x).astype(np.uint32))
+    segs.append(np.full(5000, 123456789, np.uint32))
+    segs.append(uni(6000, 200))
+    segs.append(uni(7000, 4096))
+    dup = uni(6500)
+    dup[::3] = dup[1]  # many equal keys spread through the segment
+    segs.append(dup)
+    keys = np.concatenate(segs)
+    off = np.zeros(len(segs) + 1, np.uint64)
+    off[1:] = np.cumsum([len(x) for x in segs])
+    return keys, np.arange(keys.size, dtype=np.uint32), off
+
+
+@pytest.mark.parametrize("payload", [True, False])
+def test_fine_finish_every_path(cuda_lib, payload):
+    keys, vals, off = _fine_segments(98)
+    check(cuda_lib, keys, vals if payload else None, off)
