@@ -55,6 +55,8 @@ static Tune load_tune() {
         else if (!strcmp(key, "algo")) t.algo = val;
         else if (!strcmp(key, "sweep8")) t.sweep_small = val;
         else if (!strcmp(key, "sweep11")) t.sweep_large = val;
+        else if (!strcmp(key, "sweepk")) t.sweep_keys = val;
+        else if (!strcmp(key, "heavy")) t.heavy = val;
         else if (!strcmp(key, "split")) t.split = val;
         else if (!strcmp(key, "copy_pieces")) t.copy_pieces = val;
         else if (!strcmp(key, "small")) t.small = val;
@@ -63,6 +65,7 @@ static Tune load_tune() {
         if (*p == ',') ++p;
     }
     if (t.sweep_small < 0 || t.sweep_small >= 6) t.sweep_small = 4;
+    if (t.sweep_keys < 0 || t.sweep_keys >= 6) t.sweep_keys = 3;
     if (t.sweep_large < 0 || t.sweep_large >= 4) t.sweep_large = 2;
     if (t.split < 8 || t.split > 16) t.split = 8;
     auto built = [](int sh) { return sh == 0 || sh == 1 || sh == 4 || sh == 9 || sh == 10; };

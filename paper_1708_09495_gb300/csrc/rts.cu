@@ -189,7 +189,7 @@ template <typename K>
 int autotuned_shape(const K* kin, bool vals, size_t n, int key_bits, int rb, cudaStream_t s) {
     (void)kin;
     const int bins = 1 << rb;
-    const int fixed = bins <= 256 ? tune().sweep_small : tune().sweep_large;
+    const int fixed = bins <= 256 ? (vals ? tune().sweep_small : tune().sweep_keys) : tune().sweep_large;
     AutoState& as = auto_state();
     std::lock_guard<std::mutex> lk(as.mu);
     if (!as.enabled || n < (size_t(1) << 20)) return fixed;
@@ -288,6 +288,18 @@ isort_status radix_device_rts(const K* kin, const uint32_t* vin, K* kout, uint32
     isort_status st = vals ? sweep_dispatch<K, true>(sh, true, bins, &per_sm, nullptr, 0, s)
                            : sweep_dispatch<K, false>(sh, true, bins, &per_sm, nullptr, 0, s);
     if (st != ISORT_OK) return st;
+    // pairs at the half-warp shape: every round launches the half-warp form
+    // and the per-warp-mask form of the same tile (3) back to back, and the
+    // round's digit counts pick the one that runs. Runs of repeated keys put
+    // a half-warp's 16 atomics on one ranking word; the per-warp form then
+    // takes such a warp in one step.
+    const bool dual = sh == 4 && vals && sizeof(K) == 4 && bins <= kHwBins && tune().heavy != 0 &&
+                      sweep_tile(3) == sweep_tile(4);
+    if (dual) {
+        int per_sm3 = 0;  // sets the second form's shared-memory attribute
+        st = sweep_dispatch<K, true>(3, true, bins, &per_sm3, nullptr, 0, s);
+        if (st != ISORT_OK) return st;
+    }
     const uint32_t tile = (uint32_t)sweep_tile(sh);
     const uint32_t num_tiles = (uint32_t)((n + tile - 1) / tile);
     const uint32_t want = (uint32_t)per_sm * (uint32_t)sm_count();
@@ -305,6 +317,7 @@ isort_status radix_device_rts(const K* kin, const uint32_t* vin, K* kout, uint32
     if (st != ISORT_OK) return st;
     uint32_t* status = reinterpret_cast<uint32_t*>(ws);
     unsigned long long* key_or = reinterpret_cast<unsigned long long*>(ws + 8);
+    uint32_t* heavy = reinterpret_cast<uint32_t*>(ws + 16);  // the round's digit counts have a heavy digit
     uint32_t* hist = reinterpret_cast<uint32_t*>(ws + 256);
     uint32_t* coff = reinterpret_cast<uint32_t*>(ws + 256 + align_up((size_t)chunks * bins * 4, 256));
     K* wk[2] = {nullptr, nullptr};
@@ -366,7 +379,8 @@ isort_status radix_device_rts(const K* kin, const uint32_t* vin, K* kout, uint32
             const int sbins = 1 << width;
             const int groups = sbins >= kChunkScanThreads ? 1 : kChunkScanThreads / sbins;
             k_chunk_scan<<<1, kChunkScanThreads, (size_t)(groups + 1) * sbins * 4, s>>>(
-                hist, (int)chunks, 1 << width, coff, d == 0 ? key_or : nullptr, key_bits, key_width, status);
+                hist, (int)chunks, 1 << width, coff, d == 0 ? key_or : nullptr, key_bits, key_width, status,
+                dual ? heavy : nullptr);
             ce = cudaGetLastError();
             if (ce != cudaSuccess) return fail(from_cuda(ce));
         }
@@ -385,9 +399,18 @@ isort_status radix_device_rts(const K* kin, const uint32_t* vin, K* kout, uint32
         a.status = status;
         a.limit_ns = spin_limit_ns();
         a.use_bulk = (((uintptr_t)src_k % 16) == 0) && (!vals || ((uintptr_t)src_v % 16) == 0);
+        if (dual) {
+            a.heavy = heavy;
+            a.run_if_heavy = 0;
+        }
         st = vals ? sweep_dispatch<K, true>(sh, false, a.bins, &per_sm, &a, chunks, s)
                   : sweep_dispatch<K, false>(sh, false, a.bins, &per_sm, &a, chunks, s);
         if (st != ISORT_OK) return fail(st);
+        if (dual) {
+            a.run_if_heavy = 1;
+            st = sweep_dispatch<K, true>(3, false, a.bins, &per_sm, &a, chunks, s);
+            if (st != ISORT_OK) return fail(st);
+        }
         src_k = dk;
         src_v = dv;
     }

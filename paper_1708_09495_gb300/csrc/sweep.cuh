@@ -8,6 +8,8 @@
 #include "common.cuh"
 #include "runtime.h"
 
+#include <type_traits>
+
 namespace isort {
 
 // Digit = (key >> shift) & mask. Cheap: recomputed wherever needed.
@@ -153,7 +155,8 @@ constexpr int kChunkScanThreads = 1024;
 static __global__ void __launch_bounds__(kChunkScanThreads) k_chunk_scan(const uint32_t* __restrict__ hist, int chunks,
                                                                   int bins, uint32_t* __restrict__ chunk_off,
                                                                   const unsigned long long* key_or, int key_bits,
-                                                                  int key_width, uint32_t* status) {
+                                                                  int key_width, uint32_t* status,
+                                                                  uint32_t* heavy = nullptr) {
     extern __shared__ __align__(16) uint32_t s_dyn[];  // [G][bins] group sums, then [bins] digit totals
     __shared__ uint32_t s_warp[kChunkScanThreads / 32];
     const int tid = threadIdx.x;
@@ -170,13 +173,31 @@ static __global__ void __launch_bounds__(kChunkScanThreads) k_chunk_scan(const u
         s_part[x] = t;
     }
     __syncthreads();
+    __shared__ uint32_t s_hmax[kChunkScanThreads / 32], s_hsum[kChunkScanThreads / 32];
+    uint32_t hmax = 0, hsum = 0;
     for (int d = tid; d < bins; d += kChunkScanThreads) {
         uint32_t t = 0;
         for (int g = 0; g < G; ++g) t += s_part[g * bins + d];
         s_tot[d] = t;
+        hmax = max(hmax, t);
+        hsum += t;
+    }
+    hmax = __reduce_max_sync(kFullMask, hmax);
+    hsum = __reduce_add_sync(kFullMask, hsum);
+    if ((tid & 31) == 0) {
+        s_hmax[tid >> 5] = hmax;
+        s_hsum[tid >> 5] = hsum;
     }
     __syncthreads();
     block_exclusive_scan<kChunkScanThreads>(s_tot, bins, s_warp);
+    if (heavy && tid == 0) {  // the round has a digit holding over four times its mean share of the keys
+        uint32_t m = 0, n = 0;
+        for (int w = 0; w < kChunkScanThreads / 32; ++w) {
+            m = max(m, s_hmax[w]);
+            n += s_hsum[w];
+        }
+        *heavy = (unsigned long long)m * (unsigned)bins > 4ull * n ? 1u : 0u;
+    }
     for (int x = tid; x < G * bins; x += kChunkScanThreads) {
         const int g = x / bins, d = x % bins;
         uint32_t run = s_tot[d];
@@ -207,7 +228,17 @@ struct SweepArgs {
     uint32_t* status;
     uint64_t limit_ns;
     int use_bulk;
+    // when set: the launch runs only if (*heavy != 0) == (run_if_heavy != 0)
+    // (two forms of one round launched back to back; the digit counts pick one)
+    const uint32_t* heavy = nullptr;
+    int run_if_heavy = 0;
 };
+
+// Whether this launch of a round is the form the round's digit counts picked
+// (uniform over the grid).
+__device__ __forceinline__ bool round_form_selected(const SweepArgs& a) {
+    return a.heavy == nullptr || ((*a.heavy != 0u) == (a.run_if_heavy != 0));
+}
 
 template <typename K, bool VALS, int THREADS, int ITEMS>
 struct SweepCfg {
@@ -223,7 +254,7 @@ struct SweepCfg {
         b += align_up((size_t)kWarps * bins * 2, 16);  // per-warp digit counts (u16)
         b += (size_t)kWarps * bins * 4;                // per-warp peer masks
         b += (size_t)bins * 4 * 4;                     // tile digit starts, totals, running positions, deltas
-        b += 2 * 8 + (size_t)kWarps * 4 + 16;          // mbarriers, warp sums
+        b += 2 * 8 + (size_t)kWarps * 4 + 16;          // mbarriers, warp sums, tile flags
         return align_up(b, 128);
     }
 };
@@ -241,11 +272,16 @@ template <typename K, bool VALS, int THREADS, int ITEMS, int WIDTH, bool FULL, t
 __device__ __forceinline__ void sweep_tile(const SweepArgs& a, const DF& df, K* s_keys, uint32_t* s_vals,
                                            uint16_t* s_cnt, uint32_t* s_match, uint32_t* s_start, uint32_t* s_tot,
                                            uint32_t* s_run, uint32_t* s_delta, uint32_t* s_warp_scan,
-                                           uint16_t* s_dig, uint32_t tile_n) {
+                                           uint16_t* s_dig, uint32_t* s_skew, int par, uint32_t tile_n) {
     constexpr int WARPS = THREADS / 32;
     constexpr int TILE = THREADS * ITEMS;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int bins = WIDTH > 0 ? (1 << WIDTH) : a.bins;
+    // the previous tile had a digit over four times its mean count: look for
+    // warps whose keys share one digit (flag set in the previous tile's
+    // bookkeeping; this tile's flag is cleared here, before its barrier)
+    const bool skew = s_skew[par ^ 1] != 0u;
+    if (tid == 0) s_skew[par] = 0u;
     uint16_t* my_cnt = s_cnt + warp * bins;
     uint32_t* my_match = s_match + warp * bins;
     const uint32_t lt = lanemask_lt();
@@ -253,27 +289,41 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, const DF& df, K* 
     uint32_t vreg[ITEMS];
     uint32_t rank[ITEMS];
     uint32_t dreg[ITEMS];
+    // the ranking loop in two compiled forms (the check below only where a
+    // tile before showed a heavy digit)
+    auto rank_items = [&](auto skew_c) {
+        constexpr bool SKEW = decltype(skew_c)::value;
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-        const uint32_t j = (uint32_t)(warp * ITEMS * 32 + i * 32 + lane);
-        const bool valid = FULL || j < tile_n;
-        const K k = valid ? s_keys[j] : (K)0;
-        kreg[i] = k;
-        if constexpr (VALS) vreg[i] = valid ? s_vals[j] : 0u;
-        const uint32_t d = valid ? df.digit(k) : 0u;
-        if (valid) atomicOr(&my_match[d], 1u << lane);
-        __syncwarp();
-        const uint32_t peers = valid ? my_match[d] : 0u;
-        const uint32_t c = valid ? (uint32_t)my_cnt[d] : 0u;
-        __syncwarp();
-        rank[i] = c + (uint32_t)__popc(peers & lt);
-        dreg[i] = d;
-        if (valid && (peers >> lane) == 1u) {  // the group's highest lane
-            my_cnt[d] = (uint16_t)(c + (uint32_t)__popc(peers));
-            my_match[d] = 0u;
+        for (int i = 0; i < ITEMS; ++i) {
+            const uint32_t j = (uint32_t)(warp * ITEMS * 32 + i * 32 + lane);
+            const bool valid = FULL || j < tile_n;
+            const K k = valid ? s_keys[j] : (K)0;
+            kreg[i] = k;
+            if constexpr (VALS) vreg[i] = valid ? s_vals[j] : 0u;
+            const uint32_t d = valid ? df.digit(k) : 0u;
+            // a warp whose 32 keys share one digit (runs of a repeated key) skips
+            // the mask atomics, which would all land on one word and serialize
+            bool uni = false;
+            if constexpr (SKEW) {
+                const uint32_t d0 = __shfl_sync(kFullMask, d, 0);  // every lane takes part (also invalid ones)
+                uni = __all_sync(kFullMask, valid && d == d0);
+            }
+            if (valid && !uni) atomicOr(&my_match[d], 1u << lane);
+            __syncwarp();
+            const uint32_t peers = uni ? kFullMask : (valid ? my_match[d] : 0u);
+            const uint32_t c = valid ? (uint32_t)my_cnt[d] : 0u;
+            __syncwarp();
+            rank[i] = c + (uint32_t)__popc(peers & lt);
+            dreg[i] = d;
+            if (valid && (peers >> lane) == 1u) {  // the group's highest lane
+                my_cnt[d] = (uint16_t)(c + (uint32_t)__popc(peers));
+                if (!uni) my_match[d] = 0u;
+            }
+            __syncwarp();
         }
-        __syncwarp();
-    }
+    };
+    if (skew) rank_items(std::true_type{});  // uniform over the CTA
+    else rank_items(std::false_type{});
     __syncthreads();
     for (int d = tid; d < bins; d += THREADS) {
         uint32_t sum = 0;
@@ -285,6 +335,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, const DF& df, K* 
         }
         s_start[d] = sum;
         s_tot[d] = sum;
+        if (sum * (uint32_t)bins > 4u * (uint32_t)TILE) s_skew[par] = 1u;
     }
     __syncthreads();
     block_exclusive_scan<THREADS>(s_start, bins, s_warp_scan);
@@ -329,6 +380,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, const DF& df, K* 
 template <typename K, bool VALS, int THREADS, int ITEMS, int WIDTH, typename DF>
 __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREADS) : 1)
     k_downsweep(SweepArgs a, DF df) {
+    if (!round_form_selected(a)) return;
     using Cfg = SweepCfg<K, VALS, THREADS, ITEMS>;
     constexpr int WARPS = Cfg::kWarps;
     constexpr int TILE = Cfg::kTile;
@@ -345,6 +397,7 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
     uint32_t* s_delta = s_run + bins;
     uint64_t* bars = reinterpret_cast<uint64_t*>(s_delta + bins);
     uint32_t* s_warp_scan = reinterpret_cast<uint32_t*>(bars + 2);
+    uint32_t* s_skew = s_warp_scan + WARPS;  // two tile flags (the words after the scan's)
     uint16_t* s_dig = reinterpret_cast<uint16_t*>(s_warp_scan + WARPS + 4);  // staged digits (costly digits only)
     unsigned char* s_tab = reinterpret_cast<unsigned char*>(s_dig) + (DF::kCheap ? 0 : align_up_dev((size_t)TILE * 2, 16));
     // the layout must fit the launch's shared memory (uniform check)
@@ -366,6 +419,7 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
         s_match[i] = 0;
     }
     for (int d = tid; d < bins; d += THREADS) s_run[d] = a.chunk_off[(size_t)blockIdx.x * bins + d];
+    if (tid < 2) s_skew[tid] = 0u;
     df.setup(s_tab);  // copies the digit function's tables into shared memory
     if (tid == 0) {
         mbar_init(&bars[0], 1);
@@ -415,10 +469,10 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
         }
         if (tile_n == (uint32_t)TILE)
             sweep_tile<K, VALS, THREADS, ITEMS, WIDTH, true>(a, df, s_keys, s_vals, s_cnt, s_match, s_start, s_tot,
-                                                             s_run, s_delta, s_warp_scan, s_dig, TILE);
+                                                             s_run, s_delta, s_warp_scan, s_dig, s_skew, b, TILE);
         else
             sweep_tile<K, VALS, THREADS, ITEMS, WIDTH, false>(a, df, s_keys, s_vals, s_cnt, s_match, s_start, s_tot,
-                                                              s_run, s_delta, s_warp_scan, s_dig, tile_n);
+                                                              s_run, s_delta, s_warp_scan, s_dig, s_skew, b, tile_n);
     }
 }
 
@@ -566,6 +620,7 @@ __device__ __forceinline__ void hw_tile(const SweepArgs& a, K* s_keys, uint32_t*
 template <typename K, bool VALS, int THREADS, int ITEMS>
 __global__ void __launch_bounds__(THREADS, (THREADS == 512 && ITEMS <= 8) || THREADS == 256 ? 2 : 1)
     k_downsweep_hw(SweepArgs a) {
+    if (!round_form_selected(a)) return;
     using Cfg = HwCfg<K, VALS, THREADS, ITEMS>;
     constexpr int kTile = Cfg::kTile, kBlock = Cfg::kBlock, kPitch = Cfg::kPitch, kGroups = Cfg::kGroups;
     extern __shared__ __align__(128) unsigned char smem[];

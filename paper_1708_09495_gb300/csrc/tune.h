@@ -14,12 +14,15 @@ struct Tune {
     int shape_small = 4;  // launch shape for digits of <= 8 bits
     int shape_large = 1;  // launch shape for wider digits
     int algo = 1;         // 0: single-pass rounds with look-back, 1: chunked reduce-then-scan rounds
-    int sweep_small = 4;  // chunked-round launch shape, digits of <= 8 bits (4: half-warp ranking)
+    int sweep_small = 4;  // chunked-round launch shape, digits of <= 8 bits, keys with payloads (4: half-warp ranking)
+    int sweep_keys = 3;   // chunked-round launch shape, digits of <= 8 bits, keys only (3: per-warp masks)
     int sweep_large = 2;  // chunked-round launch shape, wider digits
+    int heavy = 1;        // 1: at shape 4, a round whose digit counts have a digit over four times the mean runs
+                          // the shape-3 round instead (repeated keys; picked on the device per round)
     int small = 1;        // u32 sorts of <= 65,536 keys in place at radix 2^8: one on-chip cluster launch
-    int split = 8;
+    int split = 8;        // chunked rounds: a digit wider than this runs as two stable passes (8..16)
     int fine = 1;         // segments of <= 8,192 keys: 1 the fine finish (two 8-bit passes + runs), 0 the older kernels
-    int copy_pieces = 4;  // host-buffer staging copies: at most this many pieces on auxiliary streams        // chunked rounds: a digit wider than this runs as two stable passes (8..16)
+    int copy_pieces = 4;  // host-buffer staging copies: at most this many pieces on auxiliary streams
 };
 
 const Tune& tune();

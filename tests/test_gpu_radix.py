@@ -404,3 +404,31 @@ def test_wide_radix_against_the_paper_radix_rounds(cuda_lib, rb):
     keys[::5] = keys[11]
     vals = np.arange(n, dtype=np.uint32)
     check(cuda_lib, keys, vals, 32, rb)
+
+
+def _repeated_key_sets(n):
+    """Inputs with repeated keys: every round heavy (hashed Zipf ranks), only
+    the upper rounds heavy (three hot upper halves over uniform lower halves),
+    and long runs of one key (warps whose keys share every digit)."""
+    zipf = gen.zipf_u32(n, 1.1, 21, 3)
+    lo = gen.uniform_u32(n, 16, 22, 0)
+    hot = np.array([0x0000, 0x7A31, 0xFFFF], np.uint32)[gen.uniform_u32(n, 32, 22, 1) % 3]
+    upper = (hot << np.uint32(16)) | lo
+    runs = np.repeat(gen.uniform_u32(n // 100 + 1, 32, 23, 0), 100)[:n].copy()
+    return [("zipf", zipf), ("hot upper halves", upper), ("runs of 100", runs)]
+
+
+@pytest.mark.parametrize("payload", [True, False])
+def test_repeated_keys_both_round_forms(cuda_lib, payload):
+    """Pairs at the default shape launch two forms of each round and the
+    round's digit counts pick one (a digit over four times the mean: the
+    per-warp form); keys only take the per-warp form, whose warps with one
+    shared digit skip the mask atomics. Ragged tail, against the oracle."""
+    n = 3 * (1 << 20) + 4097
+    for name, keys in _repeated_key_sets(n):
+        vals = np.arange(n, dtype=np.uint32) if payload else None
+        ok, ov = run_radix(cuda_lib, keys, vals, 32, 8)
+        rk, rv = oracle.lsd(keys, vals, 32, 8)
+        assert np.array_equal(ok, rk), name
+        if payload:
+            assert np.array_equal(ov, rv), name
