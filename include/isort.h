@@ -322,10 +322,9 @@ ISORT_API isort_status isort_partition_u64(const uint64_t* keys_in, const uint32
  * isort_radix_noalloc: isort_radix (in place, u32 keys, optional u32 payload)
  * for callers that must not allocate memory. The paper has no counterpart; it
  * exists because some callers cannot let a library allocate device memory:
- * code that runs while a CUDA stream capture in global mode is in progress
- * (cudaMalloc is prohibited then), processes whose device memory is reserved
- * up front by another allocator, and latency-critical loops that cannot take
- * the implicit synchronisation of an allocation.
+ * processes whose device memory is reserved up front by another allocator,
+ * and latency-critical loops that cannot take the implicit synchronisation of
+ * an allocation.
  * It allocates nothing: all scratch comes from one 5 MiB array in device
  * memory that the library declares at file scope; every GPU that loads the
  * library holds that array until the process exits. Limits: n <= 262,144 keys
@@ -333,15 +332,15 @@ ISORT_API isort_status isort_partition_u64(const uint64_t* keys_in, const uint32
  * device memory (host pointers: ISORT_ERR_INVALID_ARG). Other arguments,
  * results and errors are those of isort_radix.
  * The first call on a device looks up the array's device address for that
- * device (cudaGetSymbolAddress, with the device current); make that first call
- * before any stream capture begins. All calls on a device share the array and
+ * device (cudaGetSymbolAddress, with the device current). All calls on a
+ * device share the array and
  * it keeps the last call's contents: calls whose work overlaps on the GPU
  * (different streams, or several calls enqueued in the asynchronous status
  * mode before the earlier ones finished) race and corrupt each other's
  * results. In the synchronous status mode the call waits for `stream` and
- * returns device-detected errors, except while `stream` is being captured:
- * then it returns after enqueueing and device-detected errors are recorded
- * as in the asynchronous mode (read them with isort_device_status).
+ * returns device-detected errors; on a stream that reports an active capture
+ * it does not wait, and device-detected errors are recorded as in the
+ * asynchronous mode (read them with isort_device_status).
  * ------------------------------------------------------------------------- */
 ISORT_API isort_status isort_radix_noalloc(uint32_t* keys, uint32_t* vals, size_t n, int key_bits, int radix_bits,
                                            void* stream);

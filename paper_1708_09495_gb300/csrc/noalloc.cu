@@ -1,11 +1,10 @@
 // isort_radix_noalloc: the in-place LSD radix sort for callers that must not
 // allocate memory.
 //
-// Some callers cannot let a library allocate device memory: code that runs
-// while a CUDA stream capture in global mode is in progress (cudaMalloc is
-// prohibited then), processes whose device memory is entirely reserved up
-// front by another allocator, and latency-critical loops that cannot afford
-// the implicit synchronisation an allocation may cause. For them this entry
+// Some callers cannot let a library allocate device memory: processes whose
+// device memory is entirely reserved up front by another allocator, and
+// latency-critical loops that cannot afford the implicit synchronisation an
+// allocation may cause. For them this entry
 // point takes all of its scratch from one fixed array in device memory that
 // the library declares at file scope, so no call allocates anything.
 //
@@ -87,8 +86,8 @@ isort_status isort_radix_noalloc(uint32_t* keys, uint32_t* vals, size_t n, int k
     st = radix_u32_inplace_in_workspace(keys, vals, n, key_bits, radix_bits, ws, kNoAllocScratchBytes, s, &d_status);
     if (st != ISORT_OK) return st;
     if (!sync_mode()) return finish_status(d_status, s);  // folds into the device's sticky status; no allocation
-    // A stream that is being captured cannot be waited for: the device status
-    // is then folded into the sticky word, as in the asynchronous mode.
+    // A stream that reports an active capture is not waited for: the device
+    // status is then folded into the sticky word, as in the asynchronous mode.
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     ISORT_TRY_CUDA(cudaStreamIsCapturing(s, &cap));
     if (cap != cudaStreamCaptureStatusNone) return fold_status(d_status, s);

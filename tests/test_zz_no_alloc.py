@@ -1,9 +1,9 @@
 """The allocation-free radix entry point (isort_radix_noalloc), called through
 the C ABI.
 
-Some callers cannot let a library allocate device memory (for example code
-running while a global-mode stream capture is in progress, or a process whose
-device memory is reserved up front by another allocator). This entry point
+Some callers cannot let a library allocate device memory (for example a
+process whose device memory is reserved up front by another allocator). This
+entry point
 takes its scratch from a fixed array the library declares in device memory.
 The tests check its output against the ordinary isort_radix and against the
 serial oracle, bit for bit, on calls made one after another (the shared array
