@@ -3,8 +3,8 @@ the C ABI.
 
 Some callers cannot let a library allocate device memory (for example a
 process whose device memory is reserved up front by another allocator). This
-entry point
-takes its scratch from a fixed array the library declares in device memory.
+entry point takes its scratch from a fixed array the library declares in
+device memory.
 The tests check its output against the ordinary isort_radix and against the
 serial oracle, bit for bit, on calls made one after another (the shared array
 keeps the previous call's contents, so later calls also show that what must
