@@ -524,6 +524,9 @@ def _entry(ms, n, bytes_per_key, peak, **extra):
     return e
 
 
+TUNE_CACHE = None  # --tune-cache: the autotuner's cache file for the segmented configuration
+
+
 class _Ctx:
     def __init__(self, steps, warmup):
         import torch
@@ -635,7 +638,9 @@ def cfg_segmented(c):
     # the router's cut-offs measured on this GPU (untimed), then the timed runs
     import tempfile
 
-    tune_path = os.path.join(tempfile.mkdtemp(prefix="isort_tune_"), "cache.txt")
+    # a given cache file keeps the cut-offs of an earlier run (e.g. a profiled
+    # run takes those of the plain run before it); else a fresh one is measured
+    tune_path = TUNE_CACHE or os.path.join(tempfile.mkdtemp(prefix="isort_tune_"), "cache.txt")
     c.isort.autotune(True, tune_path)
     try:
         reset_s()
@@ -830,9 +835,14 @@ def main():
                     choices=["uniform", "learned", "learned64", "segmented", "small", "radix11", "range20", "typed"],
                     help="uniform: the benchmark (with every other configuration under 'configs'); the others: "
                          "one of those configurations alone, as its own JSON line")
+    ap.add_argument("--tune-cache", default=None,
+                    help="segmented: autotuner cache file (router cut-offs read from it if present, else measured "
+                         "and written to it)")
     ap.add_argument("--dist", default="lognormal", choices=["zipf", "lognormal", "gmm", "range48"],
                     help="learned: key distribution; learned64: range48 for keys on [0, 2^48)")
     args = ap.parse_args()
+    global TUNE_CACHE
+    TUNE_CACHE = args.tune_cache
     configure(args)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

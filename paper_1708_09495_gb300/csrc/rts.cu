@@ -52,9 +52,9 @@ isort_status sweep_occupancy(int bins, int* per_sm) {
 }
 
 template <typename K, bool VALS, int THREADS, int ITEMS>
-isort_status launch_sweep(const SweepArgs& a, uint32_t chunks, cudaStream_t s) {
+isort_status launch_sweep(const SweepArgs& a, uint32_t chunks, cudaStream_t s, const char* name = "downsweep") {
     using Cfg = SweepCfg<K, VALS, THREADS, ITEMS>;
-    LaunchScope ls("downsweep", s);
+    LaunchScope ls(name, s);
     RadixDigit df;
     df.shift = a.shift;
     df.mask = (uint32_t)a.bins - 1u;
@@ -120,27 +120,29 @@ isort_status sweep_wp(bool occupancy_only, int* per_sm, const SweepArgs* a, uint
     return from_cuda(cudaGetLastError());
 }
 
+// name: the launch's name in the library's profile ("downsweep"; the second
+// form of a two-form round is "downsweep_heavy")
 template <typename K, bool VALS>
 isort_status sweep_dispatch(int sh, bool occupancy_only, int bins, int* per_sm, const SweepArgs* a, uint32_t chunks,
-                            cudaStream_t s) {
+                            cudaStream_t s, const char* name = "downsweep") {
     if constexpr (sizeof(K) == 4) {
         if (sh == 5) return sweep_wp<VALS, 512, 8, 2>(occupancy_only, per_sm, a, chunks, s);
     }
     switch (sh) {
         case 0:
             return occupancy_only ? sweep_occupancy<K, VALS, 256, 16>(bins, per_sm)
-                                  : launch_sweep<K, VALS, 256, 16>(*a, chunks, s);
+                                  : launch_sweep<K, VALS, 256, 16>(*a, chunks, s, name);
         case 1:
             return occupancy_only ? sweep_occupancy<K, VALS, 512, 16>(bins, per_sm)
-                                  : launch_sweep<K, VALS, 512, 16>(*a, chunks, s);
+                                  : launch_sweep<K, VALS, 512, 16>(*a, chunks, s, name);
         case 2:
             return occupancy_only ? sweep_occupancy<K, VALS, 256, 8>(bins, per_sm)
-                                  : launch_sweep<K, VALS, 256, 8>(*a, chunks, s);
+                                  : launch_sweep<K, VALS, 256, 8>(*a, chunks, s, name);
         case 4:
             return sweep_hw_or_generic<K, VALS, 512, 8>(occupancy_only, bins, per_sm, a, chunks, s);
         default:
             return occupancy_only ? sweep_occupancy<K, VALS, 512, 8>(bins, per_sm)
-                                  : launch_sweep<K, VALS, 512, 8>(*a, chunks, s);
+                                  : launch_sweep<K, VALS, 512, 8>(*a, chunks, s, name);
     }
 }
 
@@ -408,7 +410,7 @@ isort_status radix_device_rts(const K* kin, const uint32_t* vin, K* kout, uint32
         if (st != ISORT_OK) return fail(st);
         if (dual) {
             a.run_if_heavy = 1;
-            st = sweep_dispatch<K, true>(3, false, a.bins, &per_sm, &a, chunks, s);
+            st = sweep_dispatch<K, true>(3, false, a.bins, &per_sm, &a, chunks, s, "downsweep_heavy");
             if (st != ISORT_OK) return fail(st);
         }
         src_k = dk;
