@@ -777,7 +777,7 @@ __device__ __forceinline__ K warp_max(K x) {
 }
 
 template <typename K, bool VALS>
-__global__ void __launch_bounds__(kSegThreads, 1) k_seg_fine(SegArgsT<K> a) {
+__global__ void __launch_bounds__(kSegThreads, sizeof(K) == 4 ? 2 : 1) k_seg_fine(SegArgsT<K> a) {
     constexpr int KW = (int)sizeof(K) * 8;
     constexpr int BINS = kFineBins;
     extern __shared__ __align__(16) unsigned char smem[];
