@@ -96,6 +96,16 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
         : "memory");
 }
 
+// Asks the bulk-copy engine to bring [p, p + bytes) into L2 (a hint: nothing
+// is written, and the call returns at once). Only the 16-byte-aligned interior
+// of the range is fetched, so every address stays inside it.
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    const uintptr_t lo = (a + 15u) & ~(uintptr_t)15u, hi = (a + bytes) & ~(uintptr_t)15u;
+    if (hi > lo && hi - lo < (uintptr_t)1 << 31)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((uint32_t)(hi - lo)) : "memory");
+}
+
 // Bytes of dynamic shared memory this launch provides.
 __device__ __forceinline__ uint32_t dynamic_smem_size() {
     uint32_t v;

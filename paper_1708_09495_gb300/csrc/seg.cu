@@ -555,6 +555,15 @@ __global__ void __launch_bounds__(kSegThreads, (RB == 8 && sizeof(K) == 4) ? 2 :
         const uint64_t seg0 = a.off[s];
         const uint32_t L = (uint32_t)(a.off[s + 1] - seg0);
         const int check_bits = a.seg_bits ? KW : a.key_bits;
+        if (tid == 0 && q + nclusters < cnt) {  // this CTA's part of the cluster's next segment: into L2 meanwhile
+            const uint32_t s2 = a.list[q + nclusters];
+            const uint64_t o2 = a.off[s2], l2 = a.off[s2 + 1] - o2, lo2 = (uint64_t)r * kSegChunk;
+            if (l2 > lo2) {
+                const uint64_t n2 = min(l2 - lo2, (uint64_t)kSegChunk);
+                prefetch_l2(a.keys + o2 + lo2, n2 * sizeof(K));
+                if constexpr (VALS) prefetch_l2(a.vals + o2 + lo2, n2 * 4);
+            }
+        }
         if (tid == 0) {
             st_lo[0] = 0;
             st_len[0] = L;
@@ -811,6 +820,12 @@ __global__ void __launch_bounds__(kSegThreads, sizeof(K) == 4 ? 2 : 1) k_seg_fin
         K* gk = a.keys + seg0;
         uint32_t* gv = VALS ? a.vals + seg0 : nullptr;
         const K base = a.seg_lo ? a.seg_lo[s] : (K)0;
+        if (tid == 0 && q + gridDim.x < cnt) {  // the next segment this CTA sorts: into L2 meanwhile
+            const uint32_t s2 = a.list[q + gridDim.x];
+            const uint64_t o2 = a.off[s2], l2 = min(a.off[s2 + 1] - o2, (uint64_t)kSegChunk);
+            prefetch_l2(a.keys + o2, l2 * sizeof(K));
+            if constexpr (VALS) prefetch_l2(a.vals + o2, l2 * 4);
+        }
         const int check_bits = a.seg_bits ? KW : a.key_bits;
         if (L > (uint32_t)kSegChunk) {  // not this class's segment (never expected)
             if (tid == 0) set_status(&a.ctl->status, kStatBounds);
