@@ -83,6 +83,7 @@ constexpr uint32_t kFitStride = 8;  // the fit sees every 8th point of the sorte
 constexpr float kLearningRate = 0.002f;  // at 0.02 the first steps overshoot the quantile start (no step improved it)
 constexpr uint32_t kOnChipCapacity = 65536;  // keys a cluster finishes on chip
 constexpr int kMaxBuckets = 32768;           // the census counts every bucket in shared memory
+static_assert(kMaxBuckets <= 65536, "bucket ids are stored in 16 bits");
 
 // ---------------------------------------------------------------- sampling
 
@@ -426,6 +427,7 @@ __host__ __device__ constexpr size_t bucket_tab_bytes() {
 template <typename K>
 struct BucketDigit {
     static constexpr bool kCheap = false;
+    static constexpr bool kIndexed = false;
     const float* g_X;
     const float* g_Y;
     int B;
@@ -467,6 +469,27 @@ struct BucketDigit {
     __device__ __forceinline__ uint32_t digit(K k) const { return (bucket(k) >> sub_shift) & sub_mask; }
 };
 
+// The bucket ids the census stored (one 16-bit id per key, B <= 2^15) as the
+// digit of a distribution pass: the pass reads the id at each key's input
+// position, takes its digit, and writes the id to the key's output position
+// for the next pass (ids_out may be null on the last pass). The model is then
+// evaluated once per key, in the census, instead of once per pass.
+struct IdDigit {
+    static constexpr bool kCheap = false;
+    static constexpr bool kIndexed = true;
+    const uint16_t* ids_in;
+    uint16_t* ids_out;
+    int sub_shift;
+    uint32_t sub_mask;
+    __device__ __forceinline__ size_t table_bytes() const { return 0; }
+    __device__ __forceinline__ void setup(unsigned char*) {}
+    __device__ __forceinline__ uint32_t load(uint32_t i) const { return ids_in[i]; }
+    __device__ __forceinline__ uint32_t digit_of(uint32_t id) const { return (id >> sub_shift) & sub_mask; }
+    __device__ __forceinline__ void store(uint32_t i, uint32_t id) const {
+        if (ids_out) ids_out[i] = (uint16_t)id;
+    }
+};
+
 // Loads of a chunk: 16-byte vectors when the base allows, else scalars.
 template <typename K>
 struct KeyVec {
@@ -505,7 +528,8 @@ __global__ void __launch_bounds__(kCensusThreads) k_bucket_census(const K* __res
                                                                   uint32_t chunk_keys, BucketDigit<K> df,
                                                                   uint32_t* __restrict__ hist,
                                                                   uint32_t* __restrict__ bucket_count,
-                                                                  int key_bits, uint32_t* status, int vec) {
+                                                                  int key_bits, uint32_t* status, int vec,
+                                                                  uint16_t* __restrict__ ids = nullptr) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int bins = (int)df.sub_mask + 1;
     uint32_t* s_h = reinterpret_cast<uint32_t*>(smem);             // [bins]
@@ -516,11 +540,12 @@ __global__ void __launch_bounds__(kCensusThreads) k_bucket_census(const K* __res
     df.setup(tab);
     const uint32_t lo = blockIdx.x * chunk_keys, hi = min(n, lo + chunk_keys);
     K kor = 0;
-    for_chunk_keys<K>(keys, lo, hi, vec != 0, [&](uint32_t, K k) {
+    for_chunk_keys<K>(keys, lo, hi, vec != 0, [&](uint32_t i, K k) {
         kor |= k;
         const uint32_t b = df.bucket(k);
         atomicAdd(&s_h[(b >> df.sub_shift) & df.sub_mask], 1u);
         atomicAdd(&s_b[b], 1u);
+        if (ids) ids[i] = (uint16_t)b;  // the distribution passes read it back
     });
     __syncthreads();
     for (int i = threadIdx.x; i < bins; i += kCensusThreads) hist[(size_t)blockIdx.x * bins + i] = s_h[i];
@@ -536,29 +561,6 @@ __global__ void k_sum_columns(const uint32_t* __restrict__ in, uint32_t rows, ui
     uint32_t sum = 0;
     for (uint32_t r = 0; r < rows; ++r) sum += in[(size_t)r * cols + c];
     out[c] = sum;
-}
-
-// Per-chunk counts of a later pass's digit.
-template <typename K>
-__global__ void __launch_bounds__(kCensusThreads) k_bucket_hist(const K* __restrict__ keys, uint32_t n,
-                                                                uint32_t chunk_keys, BucketDigit<K> df,
-                                                                uint32_t* __restrict__ hist, int vec) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    constexpr int kWarps = kCensusThreads / 32;
-    const int bins = (int)df.sub_mask + 1;
-    uint32_t* s_h = reinterpret_cast<uint32_t*>(smem);  // [kWarps][bins]: one copy per warp
-    unsigned char* tab = smem + align_up_dev((size_t)kWarps * bins * 4, 16);
-    for (int i = threadIdx.x; i < kWarps * bins; i += kCensusThreads) s_h[i] = 0;
-    df.setup(tab);
-    uint32_t* my_h = s_h + (threadIdx.x >> 5) * bins;
-    const uint32_t lo = blockIdx.x * chunk_keys, hi = min(n, lo + chunk_keys);
-    for_chunk_keys<K>(keys, lo, hi, vec != 0, [&](uint32_t, K k) { atomicAdd(&my_h[df.digit(k)], 1u); });
-    __syncthreads();
-    for (int i = threadIdx.x; i < bins; i += kCensusThreads) {
-        uint32_t c = 0;
-        for (int w = 0; w < kWarps; ++w) c += s_h[w * bins + i];
-        hist[(size_t)blockIdx.x * bins + i] = c;
-    }
 }
 
 // Bucket ids of every key (the distribution passes' lookup, for checking).
@@ -609,9 +611,9 @@ struct BucketShape {
 template <typename K, bool VALS>
 isort_status bucket_sweep_setup(int bins, size_t* smem, int* per_sm) {
     using Sh = BucketShape<K>;
-    *smem = SweepCfg<K, VALS, Sh::kThreads, Sh::kItems>::smem_bytes(bins, false, bucket_tab_bytes());
+    *smem = SweepCfg<K, VALS, Sh::kThreads, Sh::kItems>::smem_bytes(bins, false, 0);
     if (*smem > max_smem_optin()) return ISORT_ERR_UNSUPPORTED;
-    auto kern = k_downsweep<K, VALS, Sh::kThreads, Sh::kItems, 0, BucketDigit<K>>;
+    auto kern = k_downsweep<K, VALS, Sh::kThreads, Sh::kItems, 0, IdDigit>;
     ISORT_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem));
     if (per_sm) {
         ISORT_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, Sh::kThreads, *smem));
@@ -621,17 +623,16 @@ isort_status bucket_sweep_setup(int bins, size_t* smem, int* per_sm) {
 }
 
 template <typename K>
-isort_status launch_bucket_sweep(const SweepArgs& a, const BucketDigit<K>& df, uint32_t chunks, bool vals,
-                                 cudaStream_t s) {
+isort_status launch_bucket_sweep(const SweepArgs& a, const IdDigit& df, uint32_t chunks, bool vals, cudaStream_t s) {
     using Sh = BucketShape<K>;
     size_t smem = 0;
     LaunchScope ls("bucket_sweep", s);
     if (vals) {
         ISORT_TRY((bucket_sweep_setup<K, true>(a.bins, &smem, nullptr)));
-        k_downsweep<K, true, Sh::kThreads, Sh::kItems, 0, BucketDigit<K>><<<chunks, Sh::kThreads, smem, s>>>(a, df);
+        k_downsweep<K, true, Sh::kThreads, Sh::kItems, 0, IdDigit><<<chunks, Sh::kThreads, smem, s>>>(a, df);
     } else {
         ISORT_TRY((bucket_sweep_setup<K, false>(a.bins, &smem, nullptr)));
-        k_downsweep<K, false, Sh::kThreads, Sh::kItems, 0, BucketDigit<K>><<<chunks, Sh::kThreads, smem, s>>>(a, df);
+        k_downsweep<K, false, Sh::kThreads, Sh::kItems, 0, IdDigit><<<chunks, Sh::kThreads, smem, s>>>(a, df);
     }
     return from_cuda(cudaGetLastError());
 }
@@ -682,6 +683,7 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
     const size_t o_hist = take((size_t)chunks * bins * 4), o_coff = take((size_t)chunks * bins * 4);
     const size_t o_segoff = take((size_t)(B + 1) * 8), o_seglo = take((size_t)B * sizeof(K)), o_segbits = take((size_t)B);
     const size_t o_buf = take(n * sizeof(K) + (hv ? align_up(n * 4, 256) : 0));
+    const size_t o_ids = take(2 * align_up(n * 2, 256));  // bucket ids: the census's, then the first pass's output
     unsigned char* ws = nullptr;
     isort_status st = scratch_alloc((void**)&ws, off, s);
     if (st != ISORT_OK) return st;
@@ -706,6 +708,8 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
     uint8_t* segbits = reinterpret_cast<uint8_t*>(ws + o_segbits);
     K* wk = reinterpret_cast<K*>(ws + o_buf);
     uint32_t* wv = hv ? reinterpret_cast<uint32_t*>(ws + o_buf + align_up(n * sizeof(K), 256)) : nullptr;
+    uint16_t* ids[2] = {reinterpret_cast<uint16_t*>(ws + o_ids),
+                        reinterpret_cast<uint16_t*>(ws + o_ids + align_up(n * 2, 256))};
 
     cudaError_t ce = cudaMemsetAsync(ws, 0, 128, s);
     if (ce != cudaSuccess) return fail(from_cuda(ce));
@@ -761,7 +765,7 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
         if (ce != cudaSuccess) return fail(from_cuda(ce));
         LaunchScope ls("bucket_census", s);
         k_bucket_census<K><<<chunks, kCensusThreads, smem, s>>>(keys, (uint32_t)n, chunk_tiles * tile, df, hist, bpart,
-                                                              key_bits, status, vec);
+                                                              key_bits, status, vec, ids[0]);
         k_sum_columns<<<(B + 255) / 256, 256, 0, s>>>(bpart, chunks, (uint32_t)B, bcount);
         ce = cudaGetLastError();
         if (ce != cudaSuccess) return fail(from_cuda(ce));
@@ -800,24 +804,30 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
         return st;
     }
 
-    // 5. stable distribution by bucket id (LSD over its halves)
+    // 5. stable distribution by bucket id (LSD over its halves); the ids the
+    // census stored move with their keys (IdDigit), so the model is not
+    // evaluated again
     K* src_k = keys;
     uint32_t* src_v = vals;
     for (int p = 0; p < passes; ++p) {
         const bool to_buf = (p % 2) == 0;
         K* dk = to_buf ? wk : keys;
         uint32_t* dv = to_buf ? wv : vals;
-        df.sub_shift = p * wsub;
-        df.sub_mask = (uint32_t)((1 << std::min(wsub, id_bits - p * wsub)) - 1);
-        const int pbins = (int)df.sub_mask + 1;
-        if (p > 0) {
-            const size_t smem = align_up((size_t)(kCensusThreads / 32) * pbins * 4, 16) + tb;
-            ce = cudaFuncSetAttribute(k_bucket_hist<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        IdDigit idf;
+        idf.ids_in = ids[p];
+        idf.ids_out = p + 1 < passes ? ids[p + 1] : nullptr;
+        idf.sub_shift = p * wsub;
+        idf.sub_mask = (uint32_t)((1 << std::min(wsub, id_bits - p * wsub)) - 1);
+        const int pbins = (int)idf.sub_mask + 1;
+        if (p > 0) {  // per-chunk counts of this pass's digit, from the moved ids
+            constexpr int kIdSub = 16;
+            const size_t smem = (size_t)kIdSub * pbins * 4;
+            ce = cudaFuncSetAttribute(k_chunk_hist<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (ce != cudaSuccess) return fail(from_cuda(ce));
             LaunchScope ls("bucket_hist", s);
-            const int pvec = ((uintptr_t)src_k % 16) == 0 ? 1 : 0;
-            k_bucket_hist<K><<<chunks, kCensusThreads, smem, s>>>(src_k, (uint32_t)n, chunk_tiles * tile, df, hist,
-                                                                pvec);
+            k_chunk_hist<uint16_t><<<chunks, kChunkHistThreads, smem, s>>>(
+                ids[p], (uint32_t)n, idf.sub_shift, ceil_log2((uint32_t)pbins), chunk_tiles * tile, kIdSub, hist,
+                nullptr, 1);
             ce = cudaGetLastError();
             if (ce != cudaSuccess) return fail(from_cuda(ce));
         }
@@ -844,7 +854,7 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
         a.status = status;
         a.limit_ns = spin_limit_ns();
         a.use_bulk = (((uintptr_t)src_k % 16) == 0) && (!hv || ((uintptr_t)src_v % 16) == 0);
-        st = launch_bucket_sweep<K>(a, df, chunks, hv, s);
+        st = launch_bucket_sweep<K>(a, idf, chunks, hv, s);
         if (st != ISORT_OK) return fail(st);
         src_k = dk;
         src_v = dv;

@@ -38,6 +38,7 @@ __global__ void k_sample(const K* __restrict__ keys, uint64_t n, uint32_t m, uin
 template <typename K>
 struct RangeDigit {
     static constexpr bool kCheap = false;
+    static constexpr bool kIndexed = false;
     const K* g_sample;
     uint64_t m;
     int parts;

@@ -15,6 +15,7 @@ namespace isort {
 // Digit = (key >> shift) & mask. Cheap: recomputed wherever needed.
 struct RadixDigit {
     static constexpr bool kCheap = true;
+    static constexpr bool kIndexed = false;  // the digit comes from the key (see sweep_tile)
     int shift;
     uint32_t mask;
     __device__ __forceinline__ size_t table_bytes() const { return 0; }
@@ -114,6 +115,14 @@ __global__ void __launch_bounds__(kChunkHistThreads) k_chunk_hist(const K* __res
                 for (int e = 0; e < 4; ++e) {
                     acc |= (K)w[e];
                     atomicAdd(&my[(w[e] >> shift) & mask], 1u);
+                }
+            } else if constexpr (sizeof(K) == 2) {
+                const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const uint32_t x = (w[e >> 1] >> ((e & 1) * 16)) & 0xFFFFu;
+                    acc |= (K)x;
+                    atomicAdd(&my[(x >> shift) & mask], 1u);
                 }
             } else {
                 const K w[2] = {((K)v.y << 32) | v.x, ((K)v.w << 32) | v.z};
@@ -272,7 +281,8 @@ template <typename K, bool VALS, int THREADS, int ITEMS, int WIDTH, bool FULL, t
 __device__ __forceinline__ void sweep_tile(const SweepArgs& a, const DF& df, K* s_keys, uint32_t* s_vals,
                                            uint16_t* s_cnt, uint32_t* s_match, uint32_t* s_start, uint32_t* s_tot,
                                            uint32_t* s_run, uint32_t* s_delta, uint32_t* s_warp_scan,
-                                           uint16_t* s_dig, uint32_t* s_skew, int par, uint32_t tile_n) {
+                                           uint16_t* s_dig, uint32_t* s_skew, int par, uint32_t tile_base,
+                                           uint32_t tile_n) {
     constexpr int WARPS = THREADS / 32;
     constexpr int TILE = THREADS * ITEMS;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -291,6 +301,17 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, const DF& df, K* 
     uint32_t dreg[ITEMS];
     // the ranking loop in two compiled forms (the check below only where a
     // tile before showed a heavy digit)
+    // an indexed digit function reads a 16-bit value stored per input position
+    // (the value moves with its key; the digit is part of it): all of a
+    // thread's values are loaded before the ranking starts
+    uint32_t auxv[ITEMS];
+    if constexpr (DF::kIndexed) {
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            const uint32_t j = (uint32_t)(warp * ITEMS * 32 + i * 32 + lane);
+            auxv[i] = (FULL || j < tile_n) ? df.load(tile_base + j) : 0u;
+        }
+    }
     auto rank_items = [&](auto skew_c) {
         constexpr bool SKEW = decltype(skew_c)::value;
 #pragma unroll
@@ -300,7 +321,13 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, const DF& df, K* 
             const K k = valid ? s_keys[j] : (K)0;
             kreg[i] = k;
             if constexpr (VALS) vreg[i] = valid ? s_vals[j] : 0u;
-            const uint32_t d = valid ? df.digit(k) : 0u;
+            uint32_t d, aux = 0;
+            if constexpr (DF::kIndexed) {
+                aux = auxv[i];
+                d = valid ? df.digit_of(aux) : 0u;
+            } else {
+                d = valid ? df.digit(k) : 0u;
+            }
             // a warp whose 32 keys share one digit (runs of a repeated key) skips
             // the mask atomics, which would all land on one word and serialize
             bool uni = false;
@@ -314,7 +341,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, const DF& df, K* 
             const uint32_t c = valid ? (uint32_t)my_cnt[d] : 0u;
             __syncwarp();
             rank[i] = c + (uint32_t)__popc(peers & lt);
-            dreg[i] = d;
+            dreg[i] = DF::kIndexed ? aux : d;
             if (valid && (peers >> lane) == 1u) {  // the group's highest lane
                 my_cnt[d] = (uint16_t)(c + (uint32_t)__popc(peers));
                 if (!uni) my_match[d] = 0u;
@@ -345,12 +372,13 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, const DF& df, K* 
     for (int i = 0; i < ITEMS; ++i) {
         const uint32_t j = (uint32_t)(warp * ITEMS * 32 + i * 32 + lane);
         if (FULL || j < tile_n) {
-            const uint32_t d = dreg[i];
+            uint32_t d = dreg[i];
+            if constexpr (DF::kIndexed) d = df.digit_of(d);
             const uint32_t pos = s_start[d] + my_cnt[d] + rank[i];
             if (pos < (uint32_t)TILE) {
                 s_keys[pos] = kreg[i];
                 if constexpr (VALS) s_vals[pos] = vreg[i];
-                if constexpr (!DF::kCheap) s_dig[pos] = (uint16_t)d;
+                if constexpr (!DF::kCheap) s_dig[pos] = (uint16_t)dreg[i];  // the digit, or the indexed value
             }
         }
     }
@@ -361,11 +389,19 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, const DF& df, K* 
         const uint32_t j = (uint32_t)(tid + i * THREADS);
         if (FULL || j < tile_n) {
             const K k = s_keys[j];
-            const uint32_t d = DF::kCheap ? df.digit(k) : (uint32_t)s_dig[j];
+            uint32_t sd = 0, d;
+            if constexpr (DF::kCheap) {
+                d = df.digit(k);
+            } else {
+                sd = s_dig[j];
+                if constexpr (DF::kIndexed) d = df.digit_of(sd);
+                else d = sd;
+            }
             const uint32_t dst = s_delta[d] + j;
             if (dst < a.n) {
                 keys_out[dst] = k;
                 if constexpr (VALS) a.vals_out[dst] = s_vals[j];
+                if constexpr (DF::kIndexed) df.store(dst, sd);
             } else {
                 set_status(a.status, kStatBounds);
             }
@@ -469,10 +505,12 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
         }
         if (tile_n == (uint32_t)TILE)
             sweep_tile<K, VALS, THREADS, ITEMS, WIDTH, true>(a, df, s_keys, s_vals, s_cnt, s_match, s_start, s_tot,
-                                                             s_run, s_delta, s_warp_scan, s_dig, s_skew, b, TILE);
+                                                             s_run, s_delta, s_warp_scan, s_dig, s_skew, b, tile_base,
+                                                             TILE);
         else
             sweep_tile<K, VALS, THREADS, ITEMS, WIDTH, false>(a, df, s_keys, s_vals, s_cnt, s_match, s_start, s_tot,
-                                                              s_run, s_delta, s_warp_scan, s_dig, s_skew, b, tile_n);
+                                                              s_run, s_delta, s_warp_scan, s_dig, s_skew, b, tile_base,
+                                                              tile_n);
     }
 }
 
