@@ -756,13 +756,21 @@ constexpr int kFineThreadRun = 16;
 constexpr int kFineMaxRuns = 512;  // runs handed to warps per segment
 constexpr int kFineBins = 256;
 
+// Threads of a fine-finish CTA: 512 (two CTAs per SM) for u32 keys; 1,024 for
+// u64 keys, whose buffers leave one CTA per SM (more warps to cover latency).
+template <typename K>
+constexpr int fine_threads() {
+    return sizeof(K) == 4 ? 512 : 1024;
+}
+constexpr int kFineMisc = 256;  // words: warp minima and maxima, scan sums, flags
+
 template <typename K, bool VALS>
 constexpr size_t fine_smem_bytes() {
-    return (size_t)kSegChunk * (sizeof(K) + (VALS ? 4 : 0))  // staging
-           + (size_t)kSegWarps * kFineBins * 2                // per-warp digit counts
-           + (size_t)kSegWarps * kFineBins * 4                // per-warp peer masks
-           + (size_t)kFineBins * 4 + 128 * 4                  // digit starts, reductions and flags
-           + (size_t)kFineMaxRuns * 8;                        // long runs: start, length
+    return (size_t)kSegChunk * (sizeof(K) + (VALS ? 4 : 0))           // staging
+           + (size_t)(fine_threads<K>() / 32) * kFineBins * 2          // per-warp digit counts
+           + (size_t)(fine_threads<K>() / 32) * kFineBins * 4          // per-warp peer masks
+           + (size_t)kFineBins * 4 + kFineMisc * 4                     // digit starts, reductions and flags
+           + (size_t)kFineMaxRuns * 8;                                 // long runs: start, length
 }
 
 template <typename K>
@@ -786,21 +794,23 @@ __device__ __forceinline__ K warp_max(K x) {
 }
 
 template <typename K, bool VALS>
-__global__ void __launch_bounds__(kSegThreads, sizeof(K) == 4 ? 2 : 1) k_seg_fine(SegArgsT<K> a) {
+__global__ void __launch_bounds__(fine_threads<K>(), sizeof(K) == 4 ? 2 : 1) k_seg_fine(SegArgsT<K> a) {
     constexpr int KW = (int)sizeof(K) * 8;
     constexpr int BINS = kFineBins;
+    constexpr int FT = fine_threads<K>(), FW = FT / 32, FI = kSegChunk / FT;  // threads, warps, keys per thread
+    static_assert(FI * FT == kSegChunk && 2 * FW * (int)(sizeof(K) / 4) + FW + 2 <= kFineMisc, "fine layout");
     extern __shared__ __align__(16) unsigned char smem[];
     K* s_keys = reinterpret_cast<K*>(smem);
     uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + kSegChunk);
     uint16_t* s_cnt = reinterpret_cast<uint16_t*>(smem + (size_t)kSegChunk * (sizeof(K) + (VALS ? 4 : 0)));
-    uint32_t* s_match = reinterpret_cast<uint32_t*>(s_cnt + kSegWarps * BINS);
-    uint32_t* s_start = s_match + kSegWarps * BINS;  // [BINS]
-    uint32_t* s_misc = s_start + BINS;              // [128]: warp minima / maxima (as K), scan sums, flags
-    K* s_wmin = reinterpret_cast<K*>(s_misc);       // [16]
-    K* s_wmax = s_wmin + kSegWarps;                 // [16]
-    uint32_t* s_wsum = s_misc + 2 * kSegWarps * (int)(sizeof(K) / 4);  // [16], after the minima and maxima
-    uint32_t* s_flag = s_wsum + kSegWarps;          // [0] runs handed to warps, [1] redo
-    uint2* s_runs = reinterpret_cast<uint2*>(s_misc + 128);
+    uint32_t* s_match = reinterpret_cast<uint32_t*>(s_cnt + FW * BINS);
+    uint32_t* s_start = s_match + FW * BINS;  // [BINS]
+    uint32_t* s_misc = s_start + BINS;        // [kFineMisc]: warp minima / maxima (as K), scan sums, flags
+    K* s_wmin = reinterpret_cast<K*>(s_misc);  // [FW]
+    K* s_wmax = s_wmin + FW;                   // [FW]
+    uint32_t* s_wsum = s_misc + 2 * FW * (int)(sizeof(K) / 4);  // [FW], after the minima and maxima
+    uint32_t* s_flag = s_wsum + FW;                             // [0] runs handed to warps, [1] redo
+    uint2* s_runs = reinterpret_cast<uint2*>(s_misc + kFineMisc);
     if ((size_t)(reinterpret_cast<unsigned char*>(s_runs + kFineMaxRuns) - smem) > dynamic_smem_size()) {
         if (threadIdx.x == 0) set_status(&a.ctl->status, kStatBounds);
         return;
@@ -808,7 +818,7 @@ __global__ void __launch_bounds__(kSegThreads, sizeof(K) == 4 ? 2 : 1) k_seg_fin
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt = lanemask_lt();
     const uint32_t cnt = a.ctl->counts[a.cls];
-    for (int i = tid; i < kSegWarps * BINS; i += kSegThreads) {
+    for (int i = tid; i < FW * BINS; i += FT) {
         s_cnt[i] = 0;
         s_match[i] = 0;
     }
@@ -831,13 +841,13 @@ __global__ void __launch_bounds__(kSegThreads, sizeof(K) == 4 ? 2 : 1) k_seg_fin
             if (tid == 0) set_status(&a.ctl->status, kStatBounds);
             continue;
         }
-        // load in input order: item i of lane l of warp w is key w * 512 + 32 i + l
-        K k[kSegItems];
-        uint32_t v[kSegItems];
+        // load in input order: item i of lane l of warp w is key w * 32 FI + 32 i + l
+        K k[FI];
+        uint32_t v[FI];
         K mn = ~(K)0, mx = 0, orv = 0;
 #pragma unroll
-        for (int i = 0; i < kSegItems; ++i) {
-            const uint32_t j = (uint32_t)(warp * kSegItems * 32 + i * 32 + lane);
+        for (int i = 0; i < FI; ++i) {
+            const uint32_t j = (uint32_t)(warp * FI * 32 + i * 32 + lane);
             const bool valid = j < L;
             k[i] = valid ? gk[j] : (K)0;
             if constexpr (VALS) v[i] = valid ? gv[j] : 0u;
@@ -862,7 +872,7 @@ __global__ void __launch_bounds__(kSegThreads, sizeof(K) == 4 ? 2 : 1) k_seg_fin
         }
         mn = s_wmin[0];
         mx = s_wmax[0];
-        for (int w = 1; w < kSegWarps; ++w) {
+        for (int w = 1; w < FW; ++w) {
             const K a0 = s_wmin[w], a1 = s_wmax[w];
             mn = a0 < mn ? a0 : mn;
             mx = a1 > mx ? a1 : mx;
@@ -880,17 +890,17 @@ __global__ void __launch_bounds__(kSegThreads, sizeof(K) == 4 ? 2 : 1) k_seg_fin
         for (int pass = 0; pass < npass; ++pass) {
             if (pass == 1) {  // the first pass's order, from the staging buffer
 #pragma unroll
-                for (int i = 0; i < kSegItems; ++i) {
-                    const uint32_t j = (uint32_t)(warp * kSegItems * 32 + i * 32 + lane);
+                for (int i = 0; i < FI; ++i) {
+                    const uint32_t j = (uint32_t)(warp * FI * 32 + i * 32 + lane);
                     k[i] = j < L ? s_keys[j] : (K)0;
                     if constexpr (VALS) v[i] = j < L ? s_vals[j] : 0u;
                 }
             }
             const int dsh = t + 8 * pass;
-            uint32_t rank[kSegItems];
+            uint32_t rank[FI];
 #pragma unroll
-            for (int i = 0; i < kSegItems; ++i) {
-                const uint32_t j = (uint32_t)(warp * kSegItems * 32 + i * 32 + lane);
+            for (int i = 0; i < FI; ++i) {
+                const uint32_t j = (uint32_t)(warp * FI * 32 + i * 32 + lane);
                 const bool valid = j < L;
                 const uint32_t dg = (uint32_t)((k[i] - base - mn) >> dsh) & (uint32_t)(BINS - 1);
                 uint32_t* mw = &s_match[warp * BINS + dg];
@@ -911,7 +921,7 @@ __global__ void __launch_bounds__(kSegThreads, sizeof(K) == 4 ? 2 : 1) k_seg_fin
             if (tid < BINS) {  // per-warp counts -> per-warp exclusive prefixes; digit totals
                 uint32_t sum = 0;
 #pragma unroll 4
-                for (int w = 0; w < kSegWarps; ++w) {
+                for (int w = 0; w < FW; ++w) {
                     const uint32_t c = s_cnt[w * BINS + tid];
                     s_cnt[w * BINS + tid] = (uint16_t)sum;
                     sum += c;
@@ -920,8 +930,8 @@ __global__ void __launch_bounds__(kSegThreads, sizeof(K) == 4 ? 2 : 1) k_seg_fin
             }
             scan_bins<BINS>(s_start, s_wsum);  // synchronises
 #pragma unroll
-            for (int i = 0; i < kSegItems; ++i) {
-                const uint32_t j = (uint32_t)(warp * kSegItems * 32 + i * 32 + lane);
+            for (int i = 0; i < FI; ++i) {
+                const uint32_t j = (uint32_t)(warp * FI * 32 + i * 32 + lane);
                 if (j < L) {
                     const uint32_t dg = (uint32_t)((k[i] - base - mn) >> dsh) & (uint32_t)(BINS - 1);
                     const uint32_t p = s_start[dg] + s_cnt[warp * BINS + dg] + rank[i];
@@ -932,13 +942,13 @@ __global__ void __launch_bounds__(kSegThreads, sizeof(K) == 4 ? 2 : 1) k_seg_fin
                 }
             }
             __syncthreads();
-            for (int i = tid; i < kSegWarps * BINS; i += kSegThreads) s_cnt[i] = 0;
+            for (int i = tid; i < FW * BINS; i += FT) s_cnt[i] = 0;
             __syncthreads();  // cleared before the next pass (or segment) ranks
         }
         if (t > 0) {
             // runs of keys sharing the top 16 bits, sorted on the low t bits
             const K lowmask = ((K)1 << t) - (K)1;
-            for (uint32_t j = (uint32_t)tid; j < L; j += kSegThreads) {
+            for (uint32_t j = (uint32_t)tid; j < L; j += FT) {
                 const K xj = s_keys[j] - base - mn;
                 const K dj = xj >> t;
                 if (j > 0 && ((s_keys[j - 1] - base - mn) >> t) == dj) continue;  // not a run start
@@ -979,7 +989,7 @@ __global__ void __launch_bounds__(kSegThreads, sizeof(K) == 4 ? 2 : 1) k_seg_fin
                 continue;
             }
             const uint32_t nruns = s_flag[0];
-            for (uint32_t ri = (uint32_t)warp; ri < nruns; ri += kSegWarps) {
+            for (uint32_t ri = (uint32_t)warp; ri < nruns; ri += FW) {
                 const uint2 run = s_runs[ri];
                 K* rk = s_keys + run.x;
                 uint32_t* rv = VALS ? s_vals + run.x : nullptr;
@@ -994,7 +1004,7 @@ __global__ void __launch_bounds__(kSegThreads, sizeof(K) == 4 ? 2 : 1) k_seg_fin
             }
             __syncthreads();
         }
-        for (uint32_t j = (uint32_t)tid; j < L; j += kSegThreads) {
+        for (uint32_t j = (uint32_t)tid; j < L; j += FT) {
             gk[j] = s_keys[j];
             if constexpr (VALS) gv[j] = s_vals[j];
         }
@@ -1099,10 +1109,10 @@ isort_status launch_fine(bool vals, const SegArgsT<K>& a, cudaStream_t s) {
     auto kern = vals ? k_seg_fine<K, true> : k_seg_fine<K, false>;
     ISORT_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    ISORT_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSegThreads, smem));
+    ISORT_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, fine_threads<K>(), smem));
     if (per_sm < 1) return ISORT_ERR_UNSUPPORTED;
     LaunchScope ls("seg_fine", s);
-    kern<<<per_sm * sm_count(), kSegThreads, smem, s>>>(a);
+    kern<<<per_sm * sm_count(), fine_threads<K>(), smem, s>>>(a);
     return from_cuda(cudaGetLastError());
 }
 
