@@ -432,3 +432,33 @@ def test_repeated_keys_both_round_forms(cuda_lib, payload):
         assert np.array_equal(ok, rk), name
         if payload:
             assert np.array_equal(ov, rv), name
+
+
+def test_round_form_choice_at_scale(cuda_lib):
+    """2^26 + 4,321 pairs: on hashed Zipf(1.1) ranks every round has a heavy
+    digit and the per-warp form does the rounds' work; on uniform keys the
+    half-warp form does. Both against the oracle; the library's launch
+    profile shows which form worked (the other returns at once)."""
+    import torch
+
+    n = (1 << 26) + 4321
+    vals = np.arange(n, dtype=np.uint32)
+    for name, keys, heavy in (("zipf", gen.zipf_u32(n, 1.1, 31, 0), True),
+                              ("uniform", gen.uniform_u32(n, 32, 32, 0), False)):
+        tk, tv = to_dev(keys), to_dev(vals)
+        cuda_lib.profile_read()
+        cuda_lib.profile_enable(True)
+        cuda_lib.radix(tk, tv, 32, 8)
+        torch.cuda.synchronize()
+        cuda_lib.profile_enable(False)
+        prof = cuda_lib.profile_read()
+        rk, rv = oracle.lsd(keys, vals, 32, 8)
+        assert np.array_equal(to_np(tk, np.uint32), rk), name
+        assert np.array_equal(to_np(tv, np.uint32), rv), name
+        del tk, tv
+        half_ms, per_warp_ms = prof["downsweep"][1], prof["downsweep_heavy"][1]
+        assert prof["downsweep"][0] == prof["downsweep_heavy"][0] == 4, name
+        if heavy:
+            assert per_warp_ms > 5 * half_ms, (name, prof)
+        else:
+            assert half_ms > 5 * per_warp_ms, (name, prof)
