@@ -661,6 +661,16 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
                                    : bucket_sweep_setup<K, false>(bins, &sweep_smem, &per_sm);
         if (so != ISORT_OK) return so;
     }
+    {
+        // the census runs one CTA per chunk too: no more chunks than it keeps
+        // resident, so that it runs in one wave
+        int census_per_sm = 0;
+        ISORT_TRY_CUDA(cudaFuncSetAttribute(k_bucket_census<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)census_smem));
+        ISORT_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&census_per_sm, k_bucket_census<K>,
+                                                                     kCensusThreads, census_smem));
+        if (census_per_sm >= 1) per_sm = std::min(per_sm, census_per_sm);
+    }
     const uint32_t num_tiles = (uint32_t)((n + tile - 1) / tile);
     const uint32_t want = (uint32_t)per_sm * (uint32_t)sm_count();
     const uint32_t chunk_tiles = (num_tiles + want - 1) / want;
