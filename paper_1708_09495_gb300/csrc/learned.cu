@@ -78,6 +78,33 @@ isort_status finish_buckets(uint64_t* k, uint32_t* v, const uint64_t* off, uint3
 }
 
 constexpr uint32_t kSampleSize = 1u << 16;
+
+// One segment [0, m) over key_bits bits from key 0, for the segmented finish.
+template <typename K>
+__global__ void k_one_segment(uint64_t* off, K* lo, uint8_t* bits, uint32_t m, int key_bits) {
+    off[0] = 0;
+    off[1] = m;
+    lo[0] = 0;
+    bits[0] = (uint8_t)key_bits;
+}
+
+// Sorts the sample (m <= 65,536 keys) in place: u32 keys by the plain rounds
+// (one on-chip cluster launch at this size); u64 keys as one segment of the
+// segmented finish (one cluster of CTAs, on chip) instead of 6-8 launches of
+// plain rounds. off, lo, bits: device scratch for the segment's description.
+isort_status sort_sample(uint32_t* k, uint32_t m, int key_bits, uint64_t*, uint32_t*, uint8_t*, cudaStream_t s) {
+    return plain_sort(k, nullptr, m, key_bits, s);
+}
+isort_status sort_sample(uint64_t* k, uint32_t m, int key_bits, uint64_t* off, uint64_t* lo, uint8_t* bits,
+                         cudaStream_t s) {
+    {
+        LaunchScope ls("sample_segment", s);
+        k_one_segment<uint64_t><<<1, 1, 0, s>>>(off, lo, bits, m, key_bits);
+        const cudaError_t ce = cudaGetLastError();
+        if (ce != cudaSuccess) return from_cuda(ce);
+    }
+    return finish_buckets(k, nullptr, off, 1, lo, bits, s);
+}
 constexpr uint64_t kSampleSeed = 0x5EED5EED5EEDull;
 constexpr uint32_t kFitStride = 8;  // the fit sees every 8th point of the sorted sample
 constexpr float kLearningRate = 0.002f;  // at 0.02 the first steps overshoot the quantile start (no step improved it)
@@ -731,7 +758,7 @@ isort_status learned_device(K* keys, uint32_t* vals, size_t n, int key_bits, int
         ce = cudaGetLastError();
         if (ce != cudaSuccess) return fail(from_cuda(ce));
     }
-    st = plain_sort(sample, nullptr, m, key_bits, s);
+    st = sort_sample(sample, m, key_bits, segoff, seglo, segbits, s);
     if (st != ISORT_OK) return fail(st);
 
     // 2. train the model (both leave their CDF as the table X, Y)

@@ -90,6 +90,9 @@ def test_learned_u64_uniform(cuda_lib, bits):
     keys = gen.uniform_u64((1 << 22) + 99, bits, 5, 0 if bits == 64 else 2)
     st = _u64_vs_oracle(cuda_lib, keys, key_bits=bits)
     assert not st["fell_back_to_lsd"] and st["imbalance_max_over_mean"] < 2.0
+    # the fit starts from the sorted sample's quantiles: a small loss only if
+    # the sample came out sorted (an unsorted sample puts it near 0.1)
+    assert st["train_loss_initial"] < 1e-5
 
 
 def test_learned_u64_skewed_and_keys_only(cuda_lib):
