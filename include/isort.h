@@ -199,11 +199,14 @@ ISORT_API isort_status isort_segmented(uint32_t* keys, uint32_t* vals, const uin
  *      fixed fp32 order and clamped to each segment's value range, which makes
  *      the bucket monotone in the key (buckets are key ranges); the splitter
  *      table s_b = the first key of bucket b gives each bucket's key range;
- *   4. distributes the keys stably by bucket and sorts every bucket on chip on
+ *   4. distributes the keys stably by bucket (the bucket of every key is
+ *      computed once and stored as 16 bits, which move with the key through
+ *      the two passes over the id's halves) and sorts every bucket on chip on
  *      the bits its key range spans (a bucket of one key value is skipped).
  * The output is the stable sort of the input, whatever the model learned.
  * keys (u32), vals (optional) are device memory; nbuckets 2..32768 (0 = 4096,
- * doubled up to 32768 while n / nbuckets > 16,384; for u64 keys > 8,192);
+ * doubled up to 32768 while n / nbuckets > 16,384; for u64 keys the smallest
+ * multiple of 4096 whose mean bucket holds at most 6,656 keys, up to 32768);
  * model 0 = the piecewise-linear CDF of step 2; model 1 = a 1-32-1 monotone
  * MLP CDF instead (see isort_mlp_train), trained on every 16th point of the
  * sorted sample and tabulated as the 257 knots (X_k, Y_k) steps 3-4 read;
@@ -233,7 +236,10 @@ typedef struct {
 ISORT_API isort_status isort_learned(uint32_t* keys, uint32_t* vals, size_t n, int key_bits, int nbuckets, int model,
                                      isort_learned_stats* stats, void* stream);
 /* The same for u64 keys (key_bits 1..64, 0 = 64; u = key * 2^-key_bits). The
- * buckets are finished by the on-chip split of step 4 on packed 64-bit items. */
+ * sample is sorted as one on-chip segment; buckets of up to 8,192 keys are
+ * finished by two on-chip 8-bit passes over the top 16 bits of their observed
+ * key range (runs of equal top bits then sorted on the low bits), larger ones
+ * by the on-chip split on packed 64-bit items. */
 ISORT_API isort_status isort_learned_u64(uint64_t* keys, uint32_t* vals, size_t n, int key_bits, int nbuckets,
                                          int model, isort_learned_stats* stats, void* stream);
 
