@@ -169,8 +169,12 @@ ISORT_API isort_status isort_oet_p(uint32_t* keys, uint32_t* vals, size_t n, int
  * serves all segments; each segment is routed on the device by its length to
  * OET (Section 2; <= 32 keys, one warp), BTN (Section 2, eq. Tb; <= 256 keys in
  * one warp, <= 4096 keys in one CTA) or count-sort rounds of 8-bit digits
- * (Section 3, eq. Ts) run entirely on chip by a cluster of 1, 2, 4 or 8 CTAs
- * (<= 65,536 keys). Longer segments use isort_radix's rounds, one segment at a
+ * (Section 3, eq. Ts) run entirely on chip: up to 8,192 keys by one CTA (two
+ * passes over the top 16 bits of the segment's observed key range, then runs
+ * of equal top bits sorted on the low bits), up to 65,536 keys by a cluster of
+ * 2, 4 or 8 CTAs. The cut-offs given are the built-in ones; with
+ * isort_autotune on, the network cut-offs are measured on the GPU once and
+ * cached. Longer segments use isort_radix's rounds, one segment at a
  * time; in the asynchronous status mode or while `stream` is being captured
  * they are not supported (ISORT_ERR_UNSUPPORTED recorded).
  * keys, vals (may be NULL) and seg_offsets (nseg + 1 uint64, non-decreasing)
